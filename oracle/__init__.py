@@ -48,6 +48,8 @@ def _load():
             lib.dwf_oracle_gamma.argtypes = [_dp]
             lib.dwf_oracle_dhop.argtypes = [_ip, ctypes.c_int, _ip, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_int]
+            lib.dwf_oracle_dhop_sites.argtypes = [_ip, ctypes.c_int, _ip, _dp, _dp, ctypes.POINTER(ctypes.c_long),
+                                                  ctypes.c_long, _dp, ctypes.c_int, ctypes.c_int]
             lib.dwf_oracle_mooee.argtypes = [_ip, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp, _dp,
                                              ctypes.c_int, ctypes.c_int, ctypes.c_int]
             lib.dwf_oracle_mooee.restype = ctypes.c_int
@@ -105,6 +107,20 @@ def dhop(dims, Ls, bc, U, psi, out_parity=2, dag=False, nthreads=None):
     out = np.empty_like(psi)
     _load().dwf_oracle_dhop(_ints(dims), Ls, _ints(bc), _ptr(U), _ptr(psi), _ptr(out), int(out_parity), int(dag),
                             nthreads or default_threads())
+    return out
+
+
+def dhop_sites(dims, Ls, bc, U, psi, sites, dag=False, nthreads=None):
+    """Dhop at the listed lexicographic 4D sites only: returns [len(sites), Ls, 4, 3]."""
+    U, psi = _c128(U), _c128(psi)
+    _check_spinor(dims, Ls, psi)
+    sites = np.ascontiguousarray(sites, dtype=np.int64)
+    if sites.size and (sites.min() < 0 or sites.max() >= int(np.prod(dims))):
+        raise ValueError("site index out of range")
+    out = np.empty((sites.size, Ls, 4, 3), dtype=np.complex128)
+    _load().dwf_oracle_dhop_sites(_ints(dims), Ls, _ints(bc), _ptr(U), _ptr(psi),
+                                  sites.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), sites.size, _ptr(out),
+                                  int(dag), nthreads or default_threads())
     return out
 
 

@@ -111,10 +111,58 @@ void dwf_oracle_gamma(double* out) {
 }
 
 /*
- * Wilson hopping term, applied slice by slice in s (the "node local Wilson matrix" of the
- * paper's Conclusion, acting on a 5D field). out_parity 0 or 1 computes only the output sites
- * of that parity (DhopEO for 0, DhopOE for 1; the inputs read are then automatically of the
- * other parity) and writes zero on the rest; 2 computes every site. dag selects Dhop^+.
+ * Wilson hopping term at one 4D site x, every slice s (the "node local Wilson matrix" of the
+ * paper's Conclusion, acting on a 5D field): o[s][spin][colour] = (Dhop in)(x, s), or Dhop^+.
+ */
+static void dhop_site(const geom_t* g, cplx gam[5][4][4], const cplx* U, const cplx* in, long x, int dag, cplx* o) {
+  int c[4];
+  site_coords(g, x, c);
+  /* Forward hop projector (1 - gamma), backward (1 + gamma); the adjoint swaps them. */
+  const double fwd_sign = dag ? +1.0 : -1.0;
+  const double bwd_sign = -fwd_sign;
+  for (int s = 0; s < g->Ls; ++s) {
+    cplx acc[12] = {0};
+    for (int mu = 0; mu < 4; ++mu) {
+      for (int dir = 0; dir < 2; ++dir) {
+        int cn[4] = {c[0], c[1], c[2], c[3]};
+        double phase = 1.0;
+        long link_site;
+        if (dir == 0) { /* x + mu, link U_mu(x) */
+          if (c[mu] == g->L[mu] - 1) phase = g->bc[mu];
+          cn[mu] = (c[mu] + 1) % g->L[mu];
+          link_site = x;
+        } else { /* x - mu, link U_mu(x - mu)^+ */
+          if (c[mu] == 0) phase = g->bc[mu];
+          cn[mu] = (c[mu] - 1 + g->L[mu]) % g->L[mu];
+          link_site = lex_index(g, cn);
+        }
+        const long xn = lex_index(g, cn);
+        const cplx* p = in + (xn * g->Ls + s) * 12;
+        const cplx* u = U + (link_site * 4 + mu) * 9;
+        cplx v[12];
+        for (int sp = 0; sp < 4; ++sp)
+          for (int a = 0; a < 3; ++a) {
+            cplx t = 0;
+            for (int b = 0; b < 3; ++b) t += (dir == 0 ? u[a * 3 + b] : conj(u[b * 3 + a])) * p[sp * 3 + b];
+            v[sp * 3 + a] = t;
+          }
+        const double gs = dir == 0 ? fwd_sign : bwd_sign;
+        for (int sp = 0; sp < 4; ++sp)
+          for (int a = 0; a < 3; ++a) {
+            cplx gv = 0;
+            for (int sq = 0; sq < 4; ++sq) gv += gam[mu][sp][sq] * v[sq * 3 + a];
+            acc[sp * 3 + a] += phase * (v[sp * 3 + a] + gs * gv);
+          }
+      }
+    }
+    for (int i = 0; i < 12; ++i) o[s * 12 + i] = acc[i];
+  }
+}
+
+/*
+ * Wilson hopping term on the whole lattice. out_parity 0 or 1 computes only the output sites of
+ * that parity (DhopEO for 0, DhopOE for 1; the inputs read are then automatically of the other
+ * parity) and writes zero on the rest; 2 computes every site. dag selects Dhop^+.
  */
 void dwf_oracle_dhop(const int dims[4], int Ls, const int bc[4], const double* Ud, const double* ind,
                      double* outd, int out_parity, int dag, int nthreads) {
@@ -124,9 +172,6 @@ void dwf_oracle_dhop(const int dims[4], int Ls, const int bc[4], const double* U
   const cplx* U = (const cplx*)Ud;
   const cplx* in = (const cplx*)ind;
   cplx* out = (cplx*)outd;
-  /* Forward hop projector (1 - gamma), backward (1 + gamma); the adjoint swaps them. */
-  const double fwd_sign = dag ? +1.0 : -1.0;
-  const double bwd_sign = -fwd_sign;
 #pragma omp parallel for num_threads(nthreads) schedule(static)
   for (long x = 0; x < g.V; ++x) {
     int c[4];
@@ -136,45 +181,24 @@ void dwf_oracle_dhop(const int dims[4], int Ls, const int bc[4], const double* U
       for (int i = 0; i < g.Ls * 12; ++i) o[i] = 0;
       continue;
     }
-    for (int s = 0; s < g.Ls; ++s) {
-      cplx acc[12] = {0};
-      for (int mu = 0; mu < 4; ++mu) {
-        for (int dir = 0; dir < 2; ++dir) {
-          int cn[4] = {c[0], c[1], c[2], c[3]};
-          double phase = 1.0;
-          long link_site;
-          if (dir == 0) { /* x + mu, link U_mu(x) */
-            if (c[mu] == g.L[mu] - 1) phase = g.bc[mu];
-            cn[mu] = (c[mu] + 1) % g.L[mu];
-            link_site = x;
-          } else { /* x - mu, link U_mu(x - mu)^+ */
-            if (c[mu] == 0) phase = g.bc[mu];
-            cn[mu] = (c[mu] - 1 + g.L[mu]) % g.L[mu];
-            link_site = lex_index(&g, cn);
-          }
-          const long xn = lex_index(&g, cn);
-          const cplx* p = in + (xn * g.Ls + s) * 12;
-          const cplx* u = U + (link_site * 4 + mu) * 9;
-          cplx v[12];
-          for (int sp = 0; sp < 4; ++sp)
-            for (int a = 0; a < 3; ++a) {
-              cplx t = 0;
-              for (int b = 0; b < 3; ++b)
-                t += (dir == 0 ? u[a * 3 + b] : conj(u[b * 3 + a])) * p[sp * 3 + b];
-              v[sp * 3 + a] = t;
-            }
-          const double gs = dir == 0 ? fwd_sign : bwd_sign;
-          for (int sp = 0; sp < 4; ++sp)
-            for (int a = 0; a < 3; ++a) {
-              cplx gv = 0;
-              for (int sq = 0; sq < 4; ++sq) gv += gam[mu][sp][sq] * v[sq * 3 + a];
-              acc[sp * 3 + a] += phase * (v[sp * 3 + a] + gs * gv);
-            }
-        }
-      }
-      for (int i = 0; i < 12; ++i) o[s * 12 + i] = acc[i];
-    }
+    dhop_site(&g, gam, U, in, x, dag, o);
   }
+}
+
+/*
+ * The same hopping term at a list of 4D sites only (lexicographic indices): out[k][s][spin][colour]
+ * = (Dhop in)(sites[k], s). Lets large lattices be checked, and timed, on a sample of sites.
+ */
+void dwf_oracle_dhop_sites(const int dims[4], int Ls, const int bc[4], const double* Ud, const double* ind,
+                           const long* sites, long nsites, double* outd, int dag, int nthreads) {
+  const geom_t g = make_geom(dims, Ls, bc);
+  cplx gam[5][4][4];
+  gamma_matrices(gam);
+  const cplx* U = (const cplx*)Ud;
+  const cplx* in = (const cplx*)ind;
+  cplx* out = (cplx*)outd;
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+  for (long k = 0; k < nsites; ++k) dhop_site(&g, gam, U, in, sites[k], dag, out + k * g.Ls * 12);
 }
 
 /* The (4 Ls) x (4 Ls) matrix of Mooee on one 4D site and one colour, index (s, spin). */

@@ -335,3 +335,13 @@ def test_psi_gradient_against_finite_differences(oracle_lib):
         fd = (action(psi + h * d) - action(psi - h * d)) / (2 * h)
         an = np.vdot(grad, d).real
         assert abs(fd - an) < 1e-10 * abs(an) + 1e-13 * S / h, (fd, an)
+
+
+def test_dhop_sites_matches_full_lattice(oracle_lib):
+    dims, Ls = (4, 2, 6, 4), 3
+    U = synth.random_gauge(dims, seed=141)
+    psi = synth.random_spinor(dims, Ls, seed=142)
+    sites = np.array([0, 5, 17, 63, 100, 191])
+    for dag in (False, True):
+        full = oracle_lib.dhop(dims, Ls, BC, U, psi, dag=dag).reshape(-1, Ls, 4, 3)
+        assert np.array_equal(oracle_lib.dhop_sites(dims, Ls, BC, U, psi, sites, dag=dag), full[sites])
