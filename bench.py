@@ -1,0 +1,432 @@
+"""Benchmark of the GB300 domain-wall operator: Dhop throughput against the HBM roofline, and
+plain vs mixed-precision CG time to a 1e-10 true residual.
+
+Workload (one "step"): one DhopEO + one DhopOE (a full-lattice hopping application, 1320 flops
+per 5D output site) on a 16^4 x Ls=16 lattice with weakly disordered links exp(0.3 i H),
+Gaussian spinors, M5 = 1.8, m = 0.01, antiperiodic in time. The headline `value` is the FP32
+variant; FP64, FP16- and BF16-storage variants are reported under "variants". Inputs are seeded
+synthetic fields (the paper's production gauge ensembles are not available here).
+
+L2 hygiene: each step works on one of three independent sets (operator with its own links,
+input and output fields; 3 x 221 MB in FP32), used round-robin, so every step's inputs were last
+touched two steps earlier and have been evicted from the 126 MiB L2 by the other sets' traffic.
+
+Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--no-cg]
+Under torchrun each rank runs the same workload on its own GPU (replicas: the operator has no
+data-path collective); rank 0 prints one JSON line with the aggregate over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2203_06777_gb300 import synth  # noqa: E402
+
+WORKLOAD = "dwf_16x16x16x16_ls16_exp0.3"
+CG_WORKLOAD = "dwf_24x24x24x24_ls12_exp0.4"
+FLOPS_PER_SITE = 1320
+METRIC = "DWF Dhop GFlop/s (1320 flop per 5D site) and HBM GB/s vs roofline; mixed vs FP64 CG time-to-1e-10"
+BC = (1, 1, 1, -1)
+L2_BYTES = 135_528_448
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# FP64 arithmetic ceiling of this part, measured with a DFMA throughput loop (2 flops per DFMA,
+# 152 SMs, no tensor cores): see the design notes. Dhop issues about 860 FP64 instructions per
+# 1320 flops, so its own ceiling is about 0.9 TFLOP/s.
+FP64_ALU_TFLOPS = 1.17
+
+
+def algorithmic_bytes_per_site(real_bytes: int, Ls: int) -> float:
+    """Each input spinor read once, each output written once, 8 links per 4D site amortised over Ls."""
+    return real_bytes * (24 + 24) + 8 * 18 * real_bytes / Ls
+
+
+# ---------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- distributed plumbing
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- GPU arm
+
+
+def make_sets(dwf, torch, spec, prec, nsets, seed0):
+    dims, Ls = spec["dims"], spec["Ls"]
+    sets = []
+    for k in range(nsets):
+        U = synth.random_gauge(dims, seed=1000 * spec["case"] + seed0 + 10 * k, eps=spec["eps"])
+        op = dwf.GridDWF(dims, Ls, spec["M5"], spec["mass"], bc=BC)
+        op.set_gauge(torch.from_numpy(U).cuda())
+        psi = synth.random_spinor(dims, Ls, seed=1000 * spec["case"] + seed0 + 10 * k + 1)
+        src = op.pack(torch.from_numpy(psi).cuda(), prec, dwf.FULL)
+        dst = op.field(prec, dwf.FULL, zero=True)
+        op.dhop(src, dwf.FULL, out=dst)  # converts and caches the links of this precision
+        sets.append((op, src, dst))
+    torch.cuda.synchronize()
+    return sets
+
+
+def time_dhop(dwf, torch, sets, steps, warmup, world):
+    """Time `steps` full-lattice Dhop applications (2 kernel launches each) with CUDA events."""
+    half = sets[0][0].half_reals
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        op, src, dst = sets[i % len(sets)]
+        op.dhop(src[half:], dwf.EVEN, out=dst[:half])
+        op.dhop(src[:half], dwf.ODD, out=dst[half:])
+
+    for i in range(warmup):
+        step(i)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        step(warmup + i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    return e0.elapsed_time(e1) / 1e3, 2 * steps
+
+
+def time_dhop_e2e(dwf, torch, sets, steps, warmup, world):
+    """The same Dhop through the public API with host buffers: pinned host -> device copy of the
+    input, the two half-lattice launches, device -> pinned host copy of the result, every step."""
+    op, src, dst = sets[0]
+    half = op.half_reals
+    host_in = torch.empty(src.shape, dtype=src.dtype, pin_memory=True)
+    host_in.copy_(src)
+    host_out = torch.empty(dst.shape, dtype=dst.dtype, pin_memory=True)
+    dev_in = torch.empty_like(src)
+    dev_out = torch.empty_like(dst)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        dev_in.copy_(host_in, non_blocking=True)
+        op.dhop(dev_in[half:], dwf.EVEN, out=dev_out[:half])
+        op.dhop(dev_in[:half], dwf.ODD, out=dev_out[half:])
+        host_out.copy_(dev_out, non_blocking=True)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    nbytes = src.numel() * src.element_size()
+    return e0.elapsed_time(e1) / 1e3, nbytes, dst.numel() * dst.element_size()
+
+
+def run_cg(dwf, torch, spec, maxiter=20000):
+    dims, Ls = spec["dims"], spec["Ls"]
+    U = synth.random_gauge(dims, seed=1000 * spec["case"] + 1, eps=spec["eps"])
+    op = dwf.GridDWF(dims, Ls, spec["M5"], spec["mass"], bc=BC)
+    op.set_gauge(torch.from_numpy(U).cuda())
+    b = op.pack(torch.from_numpy(synth.random_spinor(dims, Ls, seed=1000 * spec["case"] + 2)).cuda(), dwf.FP64,
+                dwf.FULL)
+    out = {}
+    x64 = None
+    for name, mode in (("fp64", dwf.CG_FP64), ("mixed_fp32", dwf.CG_MIXED_FP32), ("mixed_fp16", dwf.CG_MIXED_FP16),
+                       ("mixed_bf16", dwf.CG_MIXED_BF16)):
+        torch.cuda.synchronize()
+        x, st = op.cg(b, tol=1e-10, maxiter=maxiter, mode=mode, raise_on_fail=False)
+        torch.cuda.synchronize()
+        rec = {"seconds": round(st.seconds, 4), "iterations": st.iterations, "reliable_updates": st.reliable_updates,
+               "true_residual": st.true_residual, "converged": st.converged,
+               "dhop_gflops": round(st.flops / st.seconds / 1e9, 1)}
+        if x64 is None:
+            x64 = x
+        else:
+            d = x - x64
+            rec["rel_err_vs_fp64_solution"] = float(torch.linalg.vector_norm(d) / torch.linalg.vector_norm(x64))
+        out[name] = rec
+    out["speedup_mixed_fp32_vs_fp64"] = round(out["fp64"]["seconds"] / out["mixed_fp32"]["seconds"], 2)
+    out["speedup_mixed_fp16_vs_fp64"] = round(out["fp64"]["seconds"] / out["mixed_fp16"]["seconds"], 2)
+    out["workload"] = CG_WORKLOAD
+    out["tol"] = 1e-10
+    op.close()
+    return out
+
+
+def cpu_baseline_sample(spec, target_seconds=10.0):
+    """The FP64 oracle as it stands, DhopEO + DhopOE on the full lattice, on all host cores."""
+    import oracle
+
+    dims, Ls = spec["dims"], spec["Ls"]
+    U = synth.random_gauge(dims, seed=1000 * spec["case"], eps=spec["eps"])
+    psi = synth.random_spinor(dims, Ls, seed=1000 * spec["case"] + 1)
+    threads = oracle.default_threads()
+    n5 = int(np.prod(dims)) // 2 * Ls
+    t0 = time.perf_counter()
+    oracle.dhop(dims, Ls, BC, U, psi, out_parity=0, nthreads=threads)
+    oracle.dhop(dims, Ls, BC, U, psi, out_parity=1, nthreads=threads)
+    first = time.perf_counter() - t0
+    reps = max(1, int(target_seconds / max(first, 1e-3)))
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.dhop(dims, Ls, BC, U, psi, out_parity=0, nthreads=threads)
+        oracle.dhop(dims, Ls, BC, U, psi, out_parity=1, nthreads=threads)
+    dt = time.perf_counter() - t0
+    gflops = FLOPS_PER_SITE * 2 * n5 * reps / dt / 1e9
+    return {"value": round(gflops, 3), "unit": "GFlop/s", "cores": threads, "kind": "oracle",
+            "sample": f"{reps} x (DhopEO + DhopOE) FP64 on the full {WORKLOAD} lattice, {dt:.1f} s"}
+
+
+def gpu_arm(args):
+    import torch
+
+    from paper_2203_06777_gb300 import dwf
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    spec = synth.WORKLOADS[WORKLOAD]
+    dims, Ls = spec["dims"], spec["Ls"]
+    n5 = int(np.prod(dims)) // 2 * Ls
+    hbm_peak, peak_kind = peaks()
+    variants = {}
+    results = {}
+    clocks = None
+    for name, prec, rb in (("f32", dwf.FP32, 4), ("f64", dwf.FP64, 8), ("f16", dwf.FP16, 2), ("bf16", dwf.BF16, 2)):
+        sets = make_sets(dwf, torch, spec, prec, 3, seed0=0)
+        steps = args.steps if name == "f32" else max(3, args.steps // (4 if name == "f64" else 1))
+        if name == "f32":
+            with ClockSampler(torch.cuda.current_device()) as cs:
+                secs, launches = time_dhop(dwf, torch, sets, steps, args.warmup, world)
+            clocks = cs.summary()
+        else:
+            secs, launches = time_dhop(dwf, torch, sets, steps, args.warmup, world)
+        secs = reduce_max(secs, world)
+        per_launch = secs / launches
+        bytes_site = algorithmic_bytes_per_site(rb, Ls)
+        gbs = bytes_site * n5 / per_launch / 1e9
+        gflops = FLOPS_PER_SITE * n5 / per_launch / 1e9
+        rec = {"gflops": round(gflops, 1), "algorithmic_gbs": round(gbs, 1),
+               "hbm_frac": round(gbs / hbm_peak, 4), "us_per_launch": round(per_launch * 1e6, 2),
+               "bytes_per_site": bytes_site, "steps": steps}
+        if name == "f64":
+            rec["alu_frac"] = round(gflops / (FP64_ALU_TFLOPS * 1e3), 4)
+            rec["bound"] = "alu"
+        results[name] = (secs, steps, launches, per_launch, gbs, gflops)
+        variants[name] = rec
+        if name == "f32":
+            e2e_secs, hb, db = time_dhop_e2e(dwf, torch, sets, max(3, args.steps // 4), args.warmup, world)
+            e2e_secs = reduce_max(e2e_secs, world)
+            e2e_steps = max(3, args.steps // 4)
+            e2e = {"value": round(world * FLOPS_PER_SITE * 2 * n5 * e2e_steps / e2e_secs / 1e9, 1), "unit": "GFlop/s",
+                   "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db}
+        for s in sets:
+            s[0].close()
+        del sets
+        torch.cuda.empty_cache()
+    secs, steps, launches, per_launch, gbs, gflops = results["f32"]
+    value = world * FLOPS_PER_SITE * 2 * n5 * steps / secs / 1e9
+    line = {
+        "metric": METRIC,
+        "value": round(value, 1),
+        "unit": "GFlop/s",
+        "n_gpus": world,
+        "steps": steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(secs / steps * 1e3, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded exp(0.3 i H) links, Gaussian spinors)",
+        "config": {"workload": WORKLOAD, "lattice": list(dims), "Ls": Ls, "M5": spec["M5"], "mass": spec["mass"],
+                   "bc": list(BC), "step": "DhopEO + DhopOE", "parallelism": f"replicas x{world}",
+                   "l2": "3 rotating operator+field sets (663 MB FP32) > L2"},
+        "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                     "frac": round(gbs / hbm_peak, 4), "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "dhop_kernel<FP32, ST=2>", "bytes_per_launch": algorithmic_bytes_per_site(4, Ls) * n5},
+        "variants": variants,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if not args.no_cg and rank == 0:
+        line["cg"] = run_cg(dwf, torch, synth.WORKLOADS[CG_WORKLOAD])
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline_sample(spec)
+    barrier(world)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- reference arm (the oracle)
+
+
+def reference_arm(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    spec = synth.WORKLOADS[WORKLOAD]
+    dims, Ls = spec["dims"], spec["Ls"]
+    U = synth.random_gauge(dims, seed=1000 * spec["case"], eps=spec["eps"])
+    psi = synth.random_spinor(dims, Ls, seed=1000 * spec["case"] + 1)
+    threads = oracle.default_threads()
+    n5 = int(np.prod(dims)) // 2 * Ls
+
+    def step():
+        oracle.dhop(dims, Ls, BC, U, psi, out_parity=0, nthreads=threads)
+        oracle.dhop(dims, Ls, BC, U, psi, out_parity=1, nthreads=threads)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = FLOPS_PER_SITE * 2 * n5 * args.steps / dt / 1e9
+    line = {"metric": METRIC, "value": round(value, 3), "unit": "GFlop/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "lattice": list(dims), "Ls": Ls, "step": "DhopEO + DhopOE"},
+            "cpu_baseline": {"value": round(value, 3), "unit": "GFlop/s", "cores": threads, "kind": "oracle",
+                             "sample": f"each step one DhopEO + DhopOE FP64 on the full {WORKLOAD} lattice"},
+            "e2e": {"value": round(value, 3), "unit": "GFlop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cg", action="store_true", help="skip the CG time-to-solution comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,149 @@
+/*
+ * grid_dwf.h -- C ABI of the GB300-native 5D domain-wall fermion operator library
+ * (libgrid_dwf.so, CUDA for sm_103a).
+ *
+ * What it computes. The paper (Boyle et al., "Grid: OneCode and FourAPIs", LATTICE2021) names
+ * the domain wall fermion (DWF) Dirac operator as the code it profiles and calls provably
+ * optimal on A100 (Introduction; Section 3, the Nsight-Systems and Nsight-Compute figures; the
+ * Conclusion's node-local "Wilson" matrix). It prints no formula, so the operator here is the
+ * standard Shamir one:
+ *   Dhop psi(x,s) = sum_mu (1 - gamma_mu) U_mu(x) psi(x+mu,s) + (1 + gamma_mu) U_mu(x-mu)^+ psi(x-mu,s),
+ *   (Mooee psi)_s = (5 - M5) psi_s - P- psi_{s+1} - P+ psi_{s-1}, wrap terms +m P- psi_0 (s = Ls-1)
+ *                   and +m P+ psi_{Ls-1} (s = 0), P+- = (1 +- gamma5)/2,
+ *   M = Mooee - Dhop/2,
+ * gamma matrices in the chiral basis (mu = 0..3 <-> x, y, z, t; gamma5 = diag(1, 1, -1, -1)),
+ * boundary phase bc[mu] on hops that cross the lattice edge, checkerboard parity
+ * (x+y+z+t) mod 2, "EO" = output even / input odd, and the odd-site Schur complement
+ *   Mpc = Mooee - Moe Mooee^-1 Meo,  Meo = -D_eo/2, Moe = -D_oe/2.
+ *
+ * Conventions of the ABI.
+ *  - Every call returns int: GRID_DWF_OK (0) or a negative GRID_DWF_ERR_* code; the message of
+ *    the last failure on a handle is grid_dwf_last_error(h). No C++ exception crosses the ABI.
+ *  - Field and gauge pointers are DEVICE pointers owned by the caller, 16-byte aligned, unless a
+ *    call says otherwise. Calls are asynchronous on the handle's CUDA stream, except those that
+ *    return a host scalar (norm2, inner, cg, force), which synchronise that stream.
+ *  - Canonical layouts (FP64, complex as interleaved re, im):
+ *      spinor  [t][z][y][x][s][spin 4][colour 3]        (x fastest among the 4D coordinates),
+ *      gauge   [t][z][y][x][mu 4][a 3][b 3]              (row a, column b of U_mu(x)).
+ *  - Device field layout (what dhop/mooee/mpc/... read and write): a half field of one parity
+ *    holds V/2 checkerboard sites (cb index = lexicographic 4D index / 2); each site is one
+ *    contiguous block of Ls * 24 reals stored as [chunk][s][16 bytes], chunk = 24 reals / (16
+ *    bytes / sizeof(real)). A full field is the even half followed by the odd half.
+ *    grid_dwf_field_bytes gives the sizes; grid_dwf_pack/unpack convert from/to canonical.
+ *  - Precisions: GRID_DWF_FP64 (double storage and arithmetic), GRID_DWF_FP32 (float),
+ *    GRID_DWF_FP16 and GRID_DWF_BF16 (half / bfloat16 storage, float arithmetic).
+ *  - Aliasing: output buffers may not overlap inputs (GRID_DWF_ERR_ALIAS), except where a call
+ *    allows in-place use.
+ */
+#ifndef GRID_DWF_H
+#define GRID_DWF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct grid_dwf grid_dwf_t;
+
+enum {
+  GRID_DWF_OK = 0,
+  GRID_DWF_ERR_INVALID_ARG = -1,
+  GRID_DWF_ERR_CUDA = -2,
+  GRID_DWF_ERR_OOM = -3,
+  GRID_DWF_ERR_NOT_CONVERGED = -4,
+  GRID_DWF_ERR_NONFINITE = -5,
+  GRID_DWF_ERR_ALIAS = -6,
+  GRID_DWF_ERR_NO_GAUGE = -7
+};
+
+enum { GRID_DWF_FP64 = 0, GRID_DWF_FP32 = 1, GRID_DWF_FP16 = 2, GRID_DWF_BF16 = 3 };
+
+/* Field subsets: a half field of even or odd sites, or a full field. */
+enum { GRID_DWF_EVEN = 0, GRID_DWF_ODD = 1, GRID_DWF_FULL = 2 };
+
+/* CG modes: plain FP64, or FP64 defect correction around an inner solve whose Dirac operator and
+ * search vectors are stored in FP32, FP16 or BF16 (float arithmetic), with reliable updates. */
+enum { GRID_DWF_CG_FP64 = 0, GRID_DWF_CG_MIXED_FP32 = 1, GRID_DWF_CG_MIXED_FP16 = 2, GRID_DWF_CG_MIXED_BF16 = 3 };
+
+typedef struct {
+  int iterations;          /* inner (or plain) CG iterations */
+  int reliable_updates;    /* FP64 true-residual recomputations (mixed modes) */
+  int converged;           /* 1 if true_residual <= tol */
+  double true_residual;    /* |Mpc^+ b' - Mpc^+ Mpc x_o| / |Mpc^+ b'|, recomputed in FP64 */
+  double seconds;          /* wall time of the solve, measured on the host around the stream */
+  double flops;            /* Dhop flops performed (1320 per 5D output site per half Dhop) */
+} grid_dwf_cg_stats;
+
+/* Create an operator on an Lx x Ly x Lz x Lt x Ls lattice.
+ * dims[4] = {Lx, Ly, Lz, Lt}, each even and >= 2, Lx*Ly*Lz*Lt/2 < 2^31 / 8; 1 <= Ls <= 256;
+ * M5, mass finite, and Mooee invertible for them; bc[4] each +1 (periodic) or -1
+ * (antiperiodic), NULL meaning {+1, +1, +1, -1}; compress12 != 0 stores links as two rows (the
+ * third rebuilt as the conjugated cross product, exact for SU(3) links); stream is a
+ * cudaStream_t (NULL = legacy default stream). Uses the current CUDA device. On success *out
+ * owns device memory for the links and workspaces, freed by grid_dwf_destroy. */
+int grid_dwf_create(const int dims[4], int Ls, double M5, double mass, const int bc[4], int compress12, void* stream,
+                    grid_dwf_t** out);
+int grid_dwf_destroy(grid_dwf_t* h);
+int grid_dwf_set_stream(grid_dwf_t* h, void* stream);
+const char* grid_dwf_last_error(const grid_dwf_t* h);
+const char* grid_dwf_status_string(int code);
+
+/* Bytes of a device field of the given precision and subset (half: V/2*Ls*24 reals). */
+int grid_dwf_field_bytes(const grid_dwf_t* h, int precision, int subset, size_t* bytes);
+
+/* Upload the links. U is the canonical FP64 gauge field (host or device pointer; the library
+ * detects which). The links are stored by the handle in every precision used later (converted
+ * on first use); the boundary phase is never folded into them. */
+int grid_dwf_set_gauge(grid_dwf_t* h, const double* U);
+
+/* Canonical FP64 spinor (device, full lattice) <-> device field of `precision` for `subset`.
+ * pack reads only the canonical sites of the subset; unpack writes only those sites. */
+int grid_dwf_pack(grid_dwf_t* h, int precision, int subset, const double* canonical, void* field);
+int grid_dwf_unpack(grid_dwf_t* h, int precision, int subset, const void* field, double* canonical);
+
+/* Precision conversion of a device field: dst = scale * src (both of `subset`). */
+int grid_dwf_convert(grid_dwf_t* h, int src_precision, int dst_precision, int subset, const void* src, void* dst,
+                     double scale);
+
+/* Hopping term. parity GRID_DWF_EVEN: out (even half) = DhopEO in (odd half); GRID_DWF_ODD:
+ * out (odd) = DhopOE in (even); GRID_DWF_FULL: full fields, both halves. dag != 0: Dhop^+.
+ * 1320 flops per output 5D site. */
+int grid_dwf_dhop(grid_dwf_t* h, int precision, const void* in, void* out, int parity, int dag);
+
+/* Fifth-dimension operator on a field of `subset`: Mooee, Mooee^+ (dag), Mooee^-1 (inverse) or
+ * (Mooee^+)^-1. In-place use (in == out) is allowed. */
+int grid_dwf_mooee(grid_dwf_t* h, int precision, int subset, const void* in, void* out, int dag, int inverse);
+
+/* Full operator on full fields: out = M in, or M^+ in (dag). */
+int grid_dwf_m(grid_dwf_t* h, int precision, const void* in, void* out, int dag);
+
+/* Odd-site Schur complement on odd half fields: out = Mpc in (dag: Mpc^+ in). tmp_even: an even
+ * half field of scratch, or NULL for a handle-owned one. */
+int grid_dwf_mpc(grid_dwf_t* h, int precision, const void* in, void* out, int dag, void* tmp_even);
+
+/* out = Mpc^+ Mpc in on odd half fields. tmp_odd / tmp_even: scratch half fields or NULL. */
+int grid_dwf_mdagm(grid_dwf_t* h, int precision, const void* in, void* out, void* tmp_odd, void* tmp_even);
+
+/* Reductions with FP64 accumulation, bitwise reproducible: |a|^2, and a^+ b as (re, im). */
+int grid_dwf_norm2(grid_dwf_t* h, int precision, int subset, const void* a, double* result);
+int grid_dwf_inner(grid_dwf_t* h, int precision, int subset, const void* a, const void* b, double result[2]);
+
+/* Solve M x = b (full FP64 fields in device layout) through the odd-site Schur complement:
+ *   b'_o = b_o - Moe Mooee^-1 b_e; CG on Mpc^+ Mpc x_o = Mpc^+ b'_o; x_e = Mooee^-1 (b_e - Meo x_o).
+ * x holds the initial guess on input (its odd half is used). Stops when the FP64 true residual
+ * of the normal equations falls to tol; returns GRID_DWF_ERR_NOT_CONVERGED (x and *stats still
+ * filled) after maxiter iterations. stats may be NULL. */
+int grid_dwf_cg(grid_dwf_t* h, const void* b, void* x, double tol, int maxiter, int mode, grid_dwf_cg_stats* stats);
+
+/* S = |M psi|^2 for a full field psi (FP64 or FP32), its su(3) force F and ambient gradient
+ * G = dS/dRe U + i dS/dIm U, both canonical gauge layout FP64 device buffers (either may be
+ * NULL). chi: full field of the same precision receiving M psi, or NULL for handle-owned
+ * scratch. Under U -> exp(eps A) U with A in su(3): dS/deps = sum Re tr(A^+ F). *S_out on host. */
+int grid_dwf_force(grid_dwf_t* h, int precision, const void* psi, void* chi, double* F, double* G, double* S_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRID_DWF_H */

@@ -1,0 +1,661 @@
+// C ABI of the domain-wall operator library (declared in include/grid_dwf.h): the operator
+// handle, argument checking, the fused kernel sequences of M, Mpc and Mpc^+ Mpc, and the plain
+// and mixed-precision CG solvers, driven from the host on the handle's stream.
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+
+#include "../../include/grid_dwf.h"
+#include "dhop_kernel.cuh"
+#include "site_ops.cuh"
+
+namespace gdwf {
+cudaError_t launch_force(int prec, bool c12, const Geom& g, const void* psi, const void* chi, const void* Ue,
+                         const void* Uo, double* F, double* G, cudaStream_t st);
+}
+
+using namespace gdwf;
+
+struct grid_dwf {
+  Geom g;
+  int Ls = 0;
+  double M5 = 0, mass = 0;
+  bool c12 = false;
+  double d5 = 0, inv_d5 = 0, inv_den = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  double* U_canon = nullptr;            // canonical FP64 links, device
+  void* gauge[4][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+  std::map<int, std::pair<void*, size_t>> ws;  // workspace buffers by id
+  double* partials = nullptr;           // reduction partial sums
+  double* scal = nullptr;               // CG scalars (device)
+  double* host_scal = nullptr;          // pinned mirror of scal
+  std::string err;
+  bool sync_debug = false;
+};
+
+namespace {
+
+enum WsId : int {
+  WS_TMP_E = 0,
+  WS_TMP_O,
+  WS_TMP_E2,
+  WS_CHI,
+  WS_CG_TE,
+  WS_CG_BP,
+  WS_CG_RHS,
+  WS_CG_R,
+  WS_CG_P,
+  WS_CG_AP,
+  WS_CG_TO,
+  WS_CG_RS,
+  WS_CG_XS,
+  WS_CG_PS,
+  WS_CG_APS,
+  WS_CG_TOS,
+  WS_CG_TES,
+  WS_CANON_TMP,
+};
+
+int fail(grid_dwf_t* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+int cuda_fail(grid_dwf_t* h, cudaError_t e, const char* where) {
+  return fail(h, e == cudaErrorMemoryAllocation ? GRID_DWF_ERR_OOM : GRID_DWF_ERR_CUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(expr, where)                              \
+  do {                                               \
+    cudaError_t e_ = (expr);                         \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, where); \
+  } while (0)
+
+#define RET(expr)              \
+  do {                         \
+    int r_ = (expr);           \
+    if (r_ != GRID_DWF_OK) return r_; \
+  } while (0)
+
+bool valid_prec(int p) { return p >= GRID_DWF_FP64 && p <= GRID_DWF_BF16; }
+
+size_t half_bytes(const grid_dwf_t* h, int prec) { return (size_t)h->g.N4h * h->Ls * 24 * prec_bytes(prec); }
+
+size_t subset_bytes(const grid_dwf_t* h, int prec, int subset) {
+  return half_bytes(h, prec) * (subset == GRID_DWF_FULL ? 2 : 1);
+}
+
+int check_ptr(grid_dwf_t* h, const void* p, const char* name) {
+  if (!p) return fail(h, GRID_DWF_ERR_INVALID_ARG, std::string(name) + " is null");
+  if (reinterpret_cast<uintptr_t>(p) % 16) return fail(h, GRID_DWF_ERR_INVALID_ARG, std::string(name) + " is not 16-byte aligned");
+  return GRID_DWF_OK;
+}
+
+bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const char* x = static_cast<const char*>(a);
+  const char* y = static_cast<const char*>(b);
+  return x < y + nb && y < x + na;
+}
+
+int ws_get(grid_dwf_t* h, int id, size_t bytes, void** out) {
+  auto it = h->ws.find(id);
+  if (it != h->ws.end() && it->second.second >= bytes) {
+    *out = it->second.first;
+    return GRID_DWF_OK;
+  }
+  if (it != h->ws.end()) {
+    cudaFree(it->second.first);
+    h->ws.erase(it);
+  }
+  void* p = nullptr;
+  CK(cudaMalloc(&p, bytes), "workspace allocation");
+  h->ws[id] = {p, bytes};
+  *out = p;
+  return GRID_DWF_OK;
+}
+
+int finish(grid_dwf_t* h, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, where);
+  if (h->sync_debug) {
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, where);
+  }
+  return GRID_DWF_OK;
+}
+
+int ensure_gauge(grid_dwf_t* h, int prec) {
+  if (!h->U_canon) return fail(h, GRID_DWF_ERR_NO_GAUGE, "no gauge field set (call grid_dwf_set_gauge)");
+  if (h->gauge[prec][0]) return GRID_DWF_OK;
+  const size_t lb = link_bytes(prec_bytes(prec), h->c12);
+  const size_t bytes = (size_t)h->g.N4h * 4 * lb;
+  for (int p = 0; p < 2; ++p) CK(cudaMalloc(&h->gauge[prec][p], bytes), "gauge allocation");
+  CK(launch_pack_gauge(prec, h->c12, h->g, h->U_canon, h->gauge[prec][0], h->gauge[prec][1], h->stream), "pack gauge");
+  return GRID_DWF_OK;
+}
+
+int choose_st(int prec, int Ls) {
+  if (prec == GRID_DWF_FP64) return 1;
+  return (Ls % 2 == 0) ? 2 : 1;
+}
+
+// One half-lattice hopping application with its fused epilogue.
+int dhop_half(grid_dwf_t* h, int prec, const void* in, void* out, int out_parity, bool dag, int pre, int post,
+              double alpha, double beta, const void* aux) {
+  RET(ensure_gauge(h, prec));
+  DhopArgs a;
+  a.in = in;
+  a.out = out;
+  a.aux = aux;
+  a.Uout = h->gauge[prec][out_parity];
+  a.Uin = h->gauge[prec][1 - out_parity];
+  a.g = h->g;
+  a.out_parity = out_parity;
+  const int st = choose_st(prec, h->Ls);
+  a.nsg = h->Ls / st;
+  a.sites_per_cta = 256 / a.nsg;
+  if (a.sites_per_cta < 1) a.sites_per_cta = 1;
+  a.pre = pre;
+  a.post = post;
+  a.alpha = alpha;
+  a.beta = beta;
+  a.d5 = h->d5;
+  a.mass = h->mass;
+  a.inv_d5 = h->inv_d5;
+  a.inv_den = h->inv_den;
+  const int threads = a.nsg * a.sites_per_cta;
+  const int blocks = (h->g.N4h + a.sites_per_cta - 1) / a.sites_per_cta;
+  const size_t rbytes = prec == GRID_DWF_FP64 ? 8 : 4;
+  const size_t smem = post != POST_NONE ? (size_t)a.sites_per_cta * h->Ls * 24 * rbytes : 0;
+  cudaError_t e;
+  switch (prec) {
+    case GRID_DWF_FP64: e = launch_dhop<P64>(a, st, dag, h->c12, threads, blocks, smem, h->stream); break;
+    case GRID_DWF_FP32: e = launch_dhop<P32>(a, st, dag, h->c12, threads, blocks, smem, h->stream); break;
+    case GRID_DWF_FP16: e = launch_dhop<P16>(a, st, dag, h->c12, threads, blocks, smem, h->stream); break;
+    default: e = launch_dhop<PB16>(a, st, dag, h->c12, threads, blocks, smem, h->stream); break;
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "dhop launch");
+  return GRID_DWF_OK;
+}
+
+// out_o = Mpc in_o (dag: Mpc^+), via t_e = Mooee^-1 D_eo in and out = Mooee in - D_oe t_e / 4.
+int mpc_impl(grid_dwf_t* h, int prec, const void* in, void* out, bool dag, void* te) {
+  RET(dhop_half(h, prec, in, te, 0, dag, PRE_NONE, dag ? POST_INV_DAG : POST_INV, 1.0, 0.0, nullptr));
+  RET(dhop_half(h, prec, te, out, 1, dag, dag ? PRE_MOOEE_DAG : PRE_MOOEE, POST_NONE, -0.25, 1.0, in));
+  return GRID_DWF_OK;
+}
+
+int mdagm_impl(grid_dwf_t* h, int prec, const void* in, void* out, void* to, void* te) {
+  RET(mpc_impl(h, prec, in, to, false, te));
+  RET(mpc_impl(h, prec, to, out, true, te));
+  return GRID_DWF_OK;
+}
+
+int read_scalars(grid_dwf_t* h) {
+  CK(cudaMemcpyAsync(h->host_scal, h->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, h->stream), "scalar read");
+  CK(cudaStreamSynchronize(h->stream), "scalar read");
+  return GRID_DWF_OK;
+}
+
+int write_scalar(grid_dwf_t* h, int idx, double v) {
+  // staged through a pinned slot past the mirror so that the stream-ordered copy reads a stable value
+  h->host_scal[S_COUNT + idx] = v;
+  CK(cudaMemcpyAsync(h->scal + idx, h->host_scal + S_COUNT + idx, sizeof(double), cudaMemcpyHostToDevice, h->stream),
+     "scalar write");
+  return GRID_DWF_OK;
+}
+
+bool is_finite(double v) { return std::isfinite(v); }
+
+}  // namespace
+
+extern "C" {
+
+const char* grid_dwf_status_string(int code) {
+  switch (code) {
+    case GRID_DWF_OK: return "ok";
+    case GRID_DWF_ERR_INVALID_ARG: return "invalid argument";
+    case GRID_DWF_ERR_CUDA: return "CUDA error";
+    case GRID_DWF_ERR_OOM: return "out of device memory";
+    case GRID_DWF_ERR_NOT_CONVERGED: return "solver did not converge";
+    case GRID_DWF_ERR_NONFINITE: return "non-finite value";
+    case GRID_DWF_ERR_ALIAS: return "output overlaps an input";
+    case GRID_DWF_ERR_NO_GAUGE: return "no gauge field set";
+    default: return "unknown status";
+  }
+}
+
+const char* grid_dwf_last_error(const grid_dwf_t* h) { return h ? h->err.c_str() : "null handle"; }
+
+int grid_dwf_create(const int dims[4], int Ls, double M5, double mass, const int bc[4], int compress12, void* stream,
+                    grid_dwf_t** out) {
+  if (!out || !dims) return GRID_DWF_ERR_INVALID_ARG;
+  *out = nullptr;
+  long V = 1;
+  for (int m = 0; m < 4; ++m) {
+    if (dims[m] < 2 || dims[m] % 2) return GRID_DWF_ERR_INVALID_ARG;
+    V *= dims[m];
+  }
+  if (Ls < 1 || Ls > 256) return GRID_DWF_ERR_INVALID_ARG;
+  if ((V / 2) * 8 >= (1L << 31)) return GRID_DWF_ERR_INVALID_ARG;
+  if (!std::isfinite(M5) || !std::isfinite(mass)) return GRID_DWF_ERR_INVALID_ARG;
+  const int defbc[4] = {1, 1, 1, -1};
+  const int* b = bc ? bc : defbc;
+  for (int m = 0; m < 4; ++m)
+    if (b[m] != 1 && b[m] != -1) return GRID_DWF_ERR_INVALID_ARG;
+  const double d5 = 5.0 - M5;
+  if (d5 == 0.0) return GRID_DWF_ERR_INVALID_ARG;
+  const double den = d5 + mass * std::pow(d5, -(double)(Ls - 1));
+  // the fifth-dimension matrix has determinant d5^Ls + m per chirality
+  if (den == 0.0 || !std::isfinite(1.0 / den) || std::pow(d5, (double)Ls) + mass == 0.0) return GRID_DWF_ERR_INVALID_ARG;
+
+  grid_dwf_t* h = new grid_dwf_t();
+  Geom& g = h->g;
+  for (int m = 0; m < 4; ++m) {
+    g.L[m] = dims[m];
+    g.bc[m] = b[m];
+  }
+  g.Lxh = dims[0] / 2;
+  g.Ls = Ls;
+  g.N4h = (int)(V / 2);
+  g.stride[0] = 1;
+  g.stride[1] = g.Lxh;
+  g.stride[2] = g.Lxh * dims[1];
+  g.stride[3] = g.Lxh * dims[1] * dims[2];
+  g.div_lxh = make_fastdiv(g.Lxh);
+  g.div_ly = make_fastdiv(dims[1]);
+  g.div_lz = make_fastdiv(dims[2]);
+  h->Ls = Ls;
+  h->M5 = M5;
+  h->mass = mass;
+  h->c12 = compress12 != 0;
+  h->d5 = d5;
+  h->inv_d5 = 1.0 / d5;
+  h->inv_den = 1.0 / den;
+  h->stream = static_cast<cudaStream_t>(stream);
+  const char* sd = std::getenv("GRID_DWF_SYNC_DEBUG");
+  h->sync_debug = sd && sd[0] == '1';
+  cudaGetDevice(&h->device);
+  cudaError_t e = cudaMalloc(&h->partials, sizeof(double) * 2 * RED_BLOCKS);
+  if (e == cudaSuccess) e = cudaMalloc(&h->scal, sizeof(double) * S_COUNT);
+  if (e == cudaSuccess) e = cudaMallocHost(&h->host_scal, sizeof(double) * 2 * S_COUNT);
+  if (e == cudaSuccess) e = cudaMemset(h->scal, 0, sizeof(double) * S_COUNT);
+  if (e != cudaSuccess) {
+    grid_dwf_destroy(h);
+    return e == cudaErrorMemoryAllocation ? GRID_DWF_ERR_OOM : GRID_DWF_ERR_CUDA;
+  }
+  *out = h;
+  return GRID_DWF_OK;
+}
+
+int grid_dwf_destroy(grid_dwf_t* h) {
+  if (!h) return GRID_DWF_ERR_INVALID_ARG;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  cudaDeviceSynchronize();
+  cudaFree(h->U_canon);
+  for (auto& pp : h->gauge)
+    for (auto& q : pp) cudaFree(q);
+  for (auto& kv : h->ws) cudaFree(kv.second.first);
+  cudaFree(h->partials);
+  cudaFree(h->scal);
+  cudaFreeHost(h->host_scal);
+  delete h;
+  return GRID_DWF_OK;
+}
+
+int grid_dwf_set_stream(grid_dwf_t* h, void* stream) {
+  if (!h) return GRID_DWF_ERR_INVALID_ARG;
+  h->stream = static_cast<cudaStream_t>(stream);
+  return GRID_DWF_OK;
+}
+
+int grid_dwf_field_bytes(const grid_dwf_t* h, int precision, int subset, size_t* bytes) {
+  if (!h || !bytes || !valid_prec(precision) || subset < 0 || subset > 2) return GRID_DWF_ERR_INVALID_ARG;
+  *bytes = subset_bytes(h, precision, subset);
+  return GRID_DWF_OK;
+}
+
+int grid_dwf_set_gauge(grid_dwf_t* h, const double* U) {
+  if (!h) return GRID_DWF_ERR_INVALID_ARG;
+  if (!U) return fail(h, GRID_DWF_ERR_INVALID_ARG, "U is null");
+  const size_t bytes = (size_t)h->g.N4h * 2 * 4 * 18 * sizeof(double);
+  if (!h->U_canon) CK(cudaMalloc(&h->U_canon, bytes), "gauge allocation");
+  cudaPointerAttributes attr;
+  cudaError_t e = cudaPointerGetAttributes(&attr, U);
+  const bool on_device = e == cudaSuccess && (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged);
+  cudaGetLastError();  // clear a possible error from querying an unregistered host pointer
+  CK(cudaMemcpyAsync(h->U_canon, U, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream),
+     "gauge copy");
+  if (!on_device) CK(cudaStreamSynchronize(h->stream), "gauge copy");
+  for (int p = 0; p < 4; ++p)
+    if (h->gauge[p][0]) CK(launch_pack_gauge(p, h->c12, h->g, h->U_canon, h->gauge[p][0], h->gauge[p][1], h->stream), "pack gauge");
+  return finish(h, "set_gauge");
+}
+
+int grid_dwf_pack(grid_dwf_t* h, int precision, int subset, const double* canonical, void* field) {
+  if (!h) return GRID_DWF_ERR_INVALID_ARG;
+  if (!valid_prec(precision) || subset < 0 || subset > 2) return fail(h, GRID_DWF_ERR_INVALID_ARG, "bad precision/subset");
+  RET(check_ptr(h, canonical, "canonical"));
+  RET(check_ptr(h, field, "field"));
+  CK(launch_pack_spinor(precision, h->g, canonical, field, subset, false, h->stream), "pack");
+  return finish(h, "pack");
+}
+
+int grid_dwf_unpack(grid_dwf_t* h, int precision, int subset, const void* field, double* canonical) {
+  if (!h) return GRID_DWF_ERR_INVALID_ARG;
+  if (!valid_prec(precision) || subset < 0 || subset > 2) return fail(h, GRID_DWF_ERR_INVALID_ARG, "bad precision/subset");
+  RET(check_ptr(h, canonical, "canonical"));
+  RET(check_ptr(h, field, "field"));
+  CK(launch_pack_spinor(precision, h->g, canonical, const_cast<void*>(field), subset, true, h->stream), "unpack");
+  return finish(h, "unpack");
+}
+
+int grid_dwf_convert(grid_dwf_t* h, int src_precision, int dst_precision, int subset, const void* src, void* dst,
+                     double scale) {
+  if (!h) return GRID_DWF_ERR_INVALID_ARG;
+  if (!valid_prec(src_precision) || !valid_prec(dst_precision) || subset < 0 || subset > 2)
+    return fail(h, GRID_DWF_ERR_INVALID_ARG, "bad precision/subset");
+  RET(check_ptr(h, src, "src"));
+  RET(check_ptr(h, dst, "dst"));
+  if (overlap(src, subset_bytes(h, src_precision, subset), dst, subset_bytes(h, dst_precision, subset)) &&
+      !(src == dst && src_precision == dst_precision))
+    return fail(h, GRID_DWF_ERR_ALIAS, "convert: dst overlaps src");
+  const long nsites = (long)h->g.N4h * (subset == GRID_DWF_FULL ? 2 : 1);
+  CK(launch_convert(src_precision, dst_precision, src, dst, nsites, h->Ls, nullptr, scale, h->stream), "convert");
+  return finish(h, "convert");
+}
+
+int grid_dwf_dhop(grid_dwf_t* h, int precision, const void* in, void* out, int parity, int dag) {
+  if (!h) return GRID_DWF_ERR_INVALID_ARG;
+  if (!valid_prec(precision) || parity < 0 || parity > 2) return fail(h, GRID_DWF_ERR_INVALID_ARG, "bad precision/parity");
+  RET(check_ptr(h, in, "in"));
+  RET(check_ptr(h, out, "out"));
+  const int subset = parity == 2 ? GRID_DWF_FULL : GRID_DWF_EVEN;
+  const size_t nb = subset_bytes(h, precision, subset);
+  if (overlap(in, nb, out, nb)) return fail(h, GRID_DWF_ERR_ALIAS, "dhop: out overlaps in");
+  if (parity == 2) {
+    const size_t hb = half_bytes(h, precision);
+    const char* ic = static_cast<const char*>(in);
+    char* oc = static_cast<char*>(out);
+    RET(dhop_half(h, precision, ic + hb, oc, 0, dag != 0, PRE_NONE, POST_NONE, 1.0, 0.0, nullptr));
+    RET(dhop_half(h, precision, ic, oc + hb, 1, dag != 0, PRE_NONE, POST_NONE, 1.0, 0.0, nullptr));
+  } else {
+    RET(dhop_half(h, precision, in, out, parity, dag != 0, PRE_NONE, POST_NONE, 1.0, 0.0, nullptr));
+  }
+  return finish(h, "dhop");
+}
+
+int grid_dwf_mooee(grid_dwf_t* h, int precision, int subset, const void* in, void* out, int dag, int inverse) {
+  if (!h) return GRID_DWF_ERR_INVALID_ARG;
+  if (!valid_prec(precision) || subset < 0 || subset > 2) return fail(h, GRID_DWF_ERR_INVALID_ARG, "bad precision/subset");
+  RET(check_ptr(h, in, "in"));
+  RET(check_ptr(h, out, "out"));
+  const size_t nb = subset_bytes(h, precision, subset);
+  if (in != out && overlap(in, nb, out, nb)) return fail(h, GRID_DWF_ERR_ALIAS, "mooee: partial overlap");
+  const long nsites = (long)h->g.N4h * (subset == GRID_DWF_FULL ? 2 : 1);
+  CK(launch_mooee(precision, in, out, nsites, h->Ls, dag != 0, inverse != 0, h->d5, h->mass, h->inv_d5, h->inv_den,
+                  h->stream),
+     "mooee");
+  return finish(h, "mooee");
+}
+
+int grid_dwf_m(grid_dwf_t* h, int precision, const void* in, void* out, int dag) {
+  if (!h) return GRID_DWF_ERR_INVALID_ARG;
+  if (!valid_prec(precision)) return fail(h, GRID_DWF_ERR_INVALID_ARG, "bad precision");
+  RET(check_ptr(h, in, "in"));
+  RET(check_ptr(h, out, "out"));
+  const size_t nb = subset_bytes(h, precision, GRID_DWF_FULL);
+  if (overlap(in, nb, out, nb)) return fail(h, GRID_DWF_ERR_ALIAS, "m: out overlaps in");
+  const size_t hb = half_bytes(h, precision);
+  const char* ic = static_cast<const char*>(in);
+  char* oc = static_cast<char*>(out);
+  const int pre = dag ? PRE_MOOEE_DAG : PRE_MOOEE;
+  RET(dhop_half(h, precision, ic + hb, oc, 0, dag != 0, pre, POST_NONE, -0.5, 1.0, ic));
+  RET(dhop_half(h, precision, ic, oc + hb, 1, dag != 0, pre, POST_NONE, -0.5, 1.0, ic + hb));
+  return finish(h, "m");
+}
+
+int grid_dwf_mpc(grid_dwf_t* h, int precision, const void* in, void* out, int dag, void* tmp_even) {
+  if (!h) return GRID_DWF_ERR_INVALID_ARG;
+  if (!valid_prec(precision)) return fail(h, GRID_DWF_ERR_INVALID_ARG, "bad precision");
+  RET(check_ptr(h, in, "in"));
+  RET(check_ptr(h, out, "out"));
+  const size_t hb = half_bytes(h, precision);
+  if (overlap(in, hb, out, hb)) return fail(h, GRID_DWF_ERR_ALIAS, "mpc: out overlaps in");
+  void* te = tmp_even;
+  if (!te) RET(ws_get(h, WS_TMP_E, hb, &te));
+  RET(check_ptr(h, te, "tmp_even"));
+  if (overlap(te, hb, in, hb) || overlap(te, hb, out, hb)) return fail(h, GRID_DWF_ERR_ALIAS, "mpc: tmp overlaps");
+  RET(mpc_impl(h, precision, in, out, dag != 0, te));
+  return finish(h, "mpc");
+}
+
+int grid_dwf_mdagm(grid_dwf_t* h, int precision, const void* in, void* out, void* tmp_odd, void* tmp_even) {
+  if (!h) return GRID_DWF_ERR_INVALID_ARG;
+  if (!valid_prec(precision)) return fail(h, GRID_DWF_ERR_INVALID_ARG, "bad precision");
+  RET(check_ptr(h, in, "in"));
+  RET(check_ptr(h, out, "out"));
+  const size_t hb = half_bytes(h, precision);
+  if (overlap(in, hb, out, hb)) return fail(h, GRID_DWF_ERR_ALIAS, "mdagm: out overlaps in");
+  void* to = tmp_odd;
+  void* te = tmp_even;
+  if (!to) RET(ws_get(h, WS_TMP_O, hb, &to));
+  if (!te) RET(ws_get(h, WS_TMP_E, hb, &te));
+  RET(check_ptr(h, to, "tmp_odd"));
+  RET(check_ptr(h, te, "tmp_even"));
+  if (overlap(to, hb, in, hb) || overlap(to, hb, out, hb) || overlap(te, hb, in, hb) || overlap(te, hb, out, hb) ||
+      overlap(to, hb, te, hb))
+    return fail(h, GRID_DWF_ERR_ALIAS, "mdagm: scratch overlaps");
+  RET(mdagm_impl(h, precision, in, out, to, te));
+  return finish(h, "mdagm");
+}
+
+int grid_dwf_norm2(grid_dwf_t* h, int precision, int subset, const void* a, double* result) {
+  if (!h) return GRID_DWF_ERR_INVALID_ARG;
+  if (!valid_prec(precision) || subset < 0 || subset > 2 || !result)
+    return fail(h, GRID_DWF_ERR_INVALID_ARG, "bad precision/subset/result");
+  RET(check_ptr(h, a, "a"));
+  const long nsites = (long)h->g.N4h * (subset == GRID_DWF_FULL ? 2 : 1);
+  CK(launch_reduce(precision, a, nullptr, nsites, h->Ls, h->partials, h->scal, FIN_STORE, S_TMP0, h->stream), "norm2");
+  RET(read_scalars(h));
+  *result = h->host_scal[S_TMP0];
+  return GRID_DWF_OK;
+}
+
+int grid_dwf_inner(grid_dwf_t* h, int precision, int subset, const void* a, const void* b, double result[2]) {
+  if (!h) return GRID_DWF_ERR_INVALID_ARG;
+  if (!valid_prec(precision) || subset < 0 || subset > 2 || !result)
+    return fail(h, GRID_DWF_ERR_INVALID_ARG, "bad precision/subset/result");
+  RET(check_ptr(h, a, "a"));
+  RET(check_ptr(h, b, "b"));
+  const long nsites = (long)h->g.N4h * (subset == GRID_DWF_FULL ? 2 : 1);
+  CK(launch_reduce(precision, a, b, nsites, h->Ls, h->partials, h->scal, FIN_STORE, S_TMP0, h->stream), "inner");
+  RET(read_scalars(h));
+  result[0] = h->host_scal[S_TMP0];
+  result[1] = h->host_scal[S_TMP1];
+  return GRID_DWF_OK;
+}
+
+int grid_dwf_cg(grid_dwf_t* h, const void* b, void* x, double tol, int maxiter, int mode, grid_dwf_cg_stats* stats) {
+  if (!h) return GRID_DWF_ERR_INVALID_ARG;
+  if (mode < GRID_DWF_CG_FP64 || mode > GRID_DWF_CG_MIXED_BF16 || !(tol > 0) || maxiter < 0)
+    return fail(h, GRID_DWF_ERR_INVALID_ARG, "cg: bad mode/tol/maxiter");
+  RET(check_ptr(h, b, "b"));
+  RET(check_ptr(h, x, "x"));
+  const size_t hb = half_bytes(h, GRID_DWF_FP64);
+  if (overlap(b, 2 * hb, x, 2 * hb)) return fail(h, GRID_DWF_ERR_ALIAS, "cg: x overlaps b");
+  const auto t0 = std::chrono::steady_clock::now();
+  CK(cudaStreamSynchronize(h->stream), "cg start");
+  const long N = h->g.N4h;
+  const int Ls = h->Ls;
+  const double half_flops = 1320.0 * (double)N * Ls;
+  double flops = 0;
+  const char* be = static_cast<const char*>(b);
+  const char* bo = be + hb;
+  char* xe = static_cast<char*>(x);
+  char* xo = xe + hb;
+  void *te, *bp, *rhs, *r, *p, *Ap, *to;
+  RET(ws_get(h, WS_CG_TE, hb, &te));
+  RET(ws_get(h, WS_CG_BP, hb, &bp));
+  RET(ws_get(h, WS_CG_RHS, hb, &rhs));
+  RET(ws_get(h, WS_CG_R, hb, &r));
+  RET(ws_get(h, WS_CG_AP, hb, &Ap));
+  RET(ws_get(h, WS_CG_TO, hb, &to));
+  const int P = GRID_DWF_FP64;
+  // Schur source: b'_o = b_o + D_oe Mooee^-1 b_e / 2; rhs = Mpc^+ b'_o
+  CK(launch_mooee(P, be, te, N, Ls, false, true, h->d5, h->mass, h->inv_d5, h->inv_den, h->stream), "cg source");
+  RET(dhop_half(h, P, te, bp, 1, false, PRE_AUX, POST_NONE, 0.5, 1.0, bo));
+  RET(mpc_impl(h, P, bp, rhs, true, te));
+  flops += 3 * half_flops;
+  CK(launch_reduce(P, rhs, nullptr, N, Ls, h->partials, h->scal, FIN_STORE, S_TMP1, h->stream), "cg norm");
+  // true residual r = rhs - A x_o
+  RET(mdagm_impl(h, P, xo, Ap, to, te));
+  flops += 4 * half_flops;
+  CK(launch_residual64(rhs, Ap, r, N, Ls, h->partials, h->scal, S_RR, h->stream), "cg residual");
+  RET(read_scalars(h));
+  const double rhs_norm = std::sqrt(h->host_scal[S_TMP1]);
+  double rr = h->host_scal[S_RR];
+  if (!is_finite(rr) || !is_finite(rhs_norm)) return fail(h, GRID_DWF_ERR_NONFINITE, "cg: non-finite source or guess");
+  const double target = tol * rhs_norm;
+  int iters = 0, updates = 0;
+  bool converged = std::sqrt(rr) <= target;
+  double true_res = rhs_norm > 0 ? std::sqrt(rr) / rhs_norm : 0.0;
+  int rc = GRID_DWF_OK;
+
+  if (mode == GRID_DWF_CG_FP64) {
+    RET(ws_get(h, WS_CG_P, hb, &p));
+    CK(launch_convert(P, P, r, p, N, Ls, nullptr, 1.0, h->stream), "cg init");
+    RET(write_scalar(h, S_PSCALE, 1.0));
+    while (!converged && iters < maxiter) {
+      RET(mdagm_impl(h, P, p, Ap, to, te));
+      CK(launch_reduce(P, p, Ap, N, Ls, h->partials, h->scal, FIN_ALPHA, 0, h->stream), "cg pAp");
+      CK(launch_cg_xr(P, P, xo, r, p, Ap, N, Ls, h->partials, h->scal, h->stream), "cg update");
+      CK(launch_cg_p(P, P, r, p, N, Ls, h->scal, h->stream), "cg p");
+      flops += 4 * half_flops;
+      ++iters;
+      RET(read_scalars(h));
+      rr = h->host_scal[S_RR];
+      if (!is_finite(rr)) return fail(h, GRID_DWF_ERR_NONFINITE, "cg: non-finite residual");
+      converged = std::sqrt(rr) <= target;
+    }
+  } else {
+    const int PS = mode == GRID_DWF_CG_MIXED_FP32 ? GRID_DWF_FP32 : mode == GRID_DWF_CG_MIXED_FP16 ? GRID_DWF_FP16 : GRID_DWF_BF16;
+    const size_t hs32 = half_bytes(h, GRID_DWF_FP32), hss = half_bytes(h, PS);
+    void *rs, *xs, *ps, *aps, *tos, *tes;
+    RET(ws_get(h, WS_CG_RS, hs32, &rs));
+    RET(ws_get(h, WS_CG_XS, hs32, &xs));
+    RET(ws_get(h, WS_CG_PS, hss, &ps));
+    RET(ws_get(h, WS_CG_APS, hss, &aps));
+    RET(ws_get(h, WS_CG_TOS, hss, &tos));
+    RET(ws_get(h, WS_CG_TES, hss, &tes));
+    RET(ensure_gauge(h, PS));
+    const double nreal = (double)N * Ls * 24;
+    const double delta = 0.1;  // reliable update when |r| has dropped by this factor
+    double sigma = std::sqrt(nreal) / std::sqrt(rr);
+    CK(launch_convert(P, GRID_DWF_FP32, r, rs, N, Ls, nullptr, sigma, h->stream), "cg init");
+    CK(launch_convert(GRID_DWF_FP32, PS, rs, ps, N, Ls, nullptr, 1.0, h->stream), "cg init");
+    CK(cudaMemsetAsync(xs, 0, hs32, h->stream), "cg init");
+    CK(launch_reduce(GRID_DWF_FP32, rs, nullptr, N, Ls, h->partials, h->scal, FIN_STORE, S_RR, h->stream), "cg init");
+    RET(write_scalar(h, S_PSCALE, 1.0));
+    RET(read_scalars(h));
+    double rr_s = h->host_scal[S_RR];
+    double rr_max = rr_s;
+    while (!converged && iters < maxiter) {
+      RET(mdagm_impl(h, PS, ps, aps, tos, tes));
+      CK(launch_reduce(PS, ps, aps, N, Ls, h->partials, h->scal, FIN_ALPHA, 0, h->stream), "cg pAp");
+      CK(launch_cg_xr(GRID_DWF_FP32, PS, xs, rs, ps, aps, N, Ls, h->partials, h->scal, h->stream), "cg update");
+      flops += 4 * half_flops;
+      ++iters;
+      RET(read_scalars(h));
+      const double rr_old_s = rr_s;  // |r_s|^2 before this step (the denominator of beta)
+      rr_s = h->host_scal[S_RRNEW];
+      if (!is_finite(rr_s)) return fail(h, GRID_DWF_ERR_NONFINITE, "cg: non-finite sloppy residual");
+      const double est = std::sqrt(rr_s) / sigma;  // estimated true-scale |r|
+      if (rr_s < delta * delta * rr_max || est <= target || iters == maxiter) {
+        // reliable update: fold x_s into x, recompute the true residual in FP64, rescale
+        RET(write_scalar(h, S_TMP0, 1.0 / sigma));
+        CK(launch_accum_zero(GRID_DWF_FP32, xo, xs, N, Ls, h->scal + S_TMP0, h->stream), "cg reliable");
+        RET(mdagm_impl(h, P, xo, Ap, to, te));
+        flops += 4 * half_flops;
+        CK(launch_residual64(rhs, Ap, r, N, Ls, h->partials, h->scal, S_TMP1, h->stream), "cg reliable");
+        RET(read_scalars(h));
+        ++updates;
+        const double rr64 = h->host_scal[S_TMP1];
+        if (!is_finite(rr64)) return fail(h, GRID_DWF_ERR_NONFINITE, "cg: non-finite true residual");
+        if (std::sqrt(rr64) <= target) {
+          converged = true;
+          rr = rr64;
+          break;
+        }
+        const double sigma_new = std::sqrt(nreal) / std::sqrt(rr64);
+        CK(launch_convert(P, GRID_DWF_FP32, r, rs, N, Ls, nullptr, sigma_new, h->stream), "cg reliable");
+        CK(launch_reduce(GRID_DWF_FP32, rs, nullptr, N, Ls, h->partials, h->scal, FIN_STORE, S_RR, h->stream),
+           "cg reliable");
+        // beta (true units) = |r_true|^2 / |r_old|^2 with |r_old|^2 = rr_old_s / sigma^2; the stored
+        // p carries scale sigma and must move to sigma_new.
+        const double beta = rr64 * sigma * sigma / rr_old_s;
+        RET(write_scalar(h, S_BETA, beta * sigma_new / sigma));
+        RET(read_scalars(h));
+        rr_s = h->host_scal[S_RR];
+        rr_max = rr_s;
+        sigma = sigma_new;
+        rr = rr64;
+      }
+      CK(launch_cg_p(GRID_DWF_FP32, PS, rs, ps, N, Ls, h->scal, h->stream), "cg p");
+    }
+  }
+  // final true residual of the normal equations, FP64
+  RET(mdagm_impl(h, P, xo, Ap, to, te));
+  flops += 4 * half_flops;
+  CK(launch_residual64(rhs, Ap, r, N, Ls, h->partials, h->scal, S_TMP0, h->stream), "cg final");
+  // x_e = Mooee^-1 (b_e + D_eo x_o / 2)
+  RET(dhop_half(h, P, xo, xe, 0, false, PRE_AUX, POST_INV, 0.5, 1.0, be));
+  flops += half_flops;
+  RET(read_scalars(h));
+  true_res = rhs_norm > 0 ? std::sqrt(h->host_scal[S_TMP0]) / rhs_norm : 0.0;
+  converged = true_res <= tol;
+  if (!converged) rc = fail(h, GRID_DWF_ERR_NOT_CONVERGED, "cg: tolerance not reached within maxiter");
+  const auto t1 = std::chrono::steady_clock::now();
+  if (stats) {
+    stats->iterations = iters;
+    stats->reliable_updates = updates;
+    stats->converged = converged ? 1 : 0;
+    stats->true_residual = true_res;
+    stats->seconds = std::chrono::duration<double>(t1 - t0).count();
+    stats->flops = flops;
+  }
+  if (rc == GRID_DWF_OK) RET(finish(h, "cg"));
+  return rc;
+}
+
+int grid_dwf_force(grid_dwf_t* h, int precision, const void* psi, void* chi, double* F, double* G, double* S_out) {
+  if (!h) return GRID_DWF_ERR_INVALID_ARG;
+  if (precision != GRID_DWF_FP64 && precision != GRID_DWF_FP32)
+    return fail(h, GRID_DWF_ERR_INVALID_ARG, "force: precision must be FP64 or FP32");
+  RET(check_ptr(h, psi, "psi"));
+  const size_t fb = subset_bytes(h, precision, GRID_DWF_FULL);
+  void* c = chi;
+  if (!c) RET(ws_get(h, WS_CHI, fb, &c));
+  RET(check_ptr(h, c, "chi"));
+  if (overlap(psi, fb, c, fb)) return fail(h, GRID_DWF_ERR_ALIAS, "force: chi overlaps psi");
+  const size_t gb = (size_t)h->g.N4h * 2 * 4 * 18 * sizeof(double);
+  if (F && (overlap(F, gb, psi, fb) || overlap(F, gb, c, fb))) return fail(h, GRID_DWF_ERR_ALIAS, "force: F overlaps");
+  if (G && (overlap(G, gb, psi, fb) || overlap(G, gb, c, fb))) return fail(h, GRID_DWF_ERR_ALIAS, "force: G overlaps");
+  RET(grid_dwf_m(h, precision, psi, c, 0));
+  CK(launch_reduce(precision, c, nullptr, 2L * h->g.N4h, h->Ls, h->partials, h->scal, FIN_STORE, S_TMP0, h->stream),
+     "force action");
+  RET(ensure_gauge(h, precision));
+  if (F || G)
+    CK(launch_force(precision, h->c12, h->g, psi, c, h->gauge[precision][0], h->gauge[precision][1], F, G, h->stream),
+       "force");
+  RET(read_scalars(h));
+  if (S_out) *S_out = h->host_scal[S_TMP0];
+  return finish(h, "force");
+}
+
+}  // extern "C"

@@ -1,0 +1,180 @@
+// Derivative of the action S = |M psi|^2 with respect to the gauge links (the fermion force).
+//
+// With chi = M psi and M = Mooee - Dhop/2, only the hopping term depends on the links, so per
+// link U_mu(x), with phase the boundary factor of the hop x -> x + mu,
+//   B1 = sum_{s,spin} psi(x+mu) (x) [(1 - gamma_mu) chi(x)]^+,
+//   B2 = sum_{s,spin} psi(x)    (x) [(1 + gamma_mu) chi(x+mu)]^+           (colour outer products),
+//   G  = dS/dRe U + i dS/dIm U = -phase (B1^+ + B2)                           (ambient gradient),
+//   F  = -TA( phase (-U B1 + B2 U^+) ),  TA(X) = (X - X^+)/2 - tr(X - X^+)/6  (su(3) force),
+// so that under U -> exp(eps A) U, A in su(3), dS/deps = Re tr(A^+ F).
+// Because (1 -+ gamma_mu)/2 is a rank-2 projector, each spin sum is the sum over the two spins
+// of the projected half spinors: sum_spin a (x) [(1 - gamma) b]^+ = sum_{h=0,1} (P a)_h (x) (P b)_h^*.
+//
+// Thread mapping: nsg lanes per link (x, mu) split the Ls slices; each lane accumulates its
+// slices in the storage precision's arithmetic, the lanes are then combined in FP64 with warp
+// shuffles, and lane 0 multiplies by the link, projects and writes F and G in the canonical
+// FP64 layout [t][z][y][x][mu][3][3].
+#include "dhop_kernel.cuh"
+
+namespace gdwf {
+
+template <int P, bool C12>
+__global__ void __launch_bounds__(256) k_force(const Geom g, const char* psi, const char* chi, const char* Ue,
+                                               const char* Uo, double* F, double* G, int nsg) {
+  using T = typename Store<P>::T;
+  using R = typename Store<P>::R;
+  constexpr int LB = link_bytes(sizeof(T), C12);
+  const int Ls = g.Ls;
+  const size_t site_bytes = (size_t)Ls * 24 * sizeof(T);
+  const size_t half_bytes = (size_t)g.N4h * site_bytes;
+  const int lane = threadIdx.x % nsg;
+  const long link = (long)blockIdx.x * (blockDim.x / nsg) + threadIdx.x / nsg;
+  const bool active = link < 8L * g.N4h;
+  const int mu = (int)(link & 3);
+  const long rest = link >> 2;
+  const int p = rest >= g.N4h ? 1 : 0;
+  const int i = (int)(rest - (long)p * g.N4h);
+
+  R b1[18], b2[18];
+#pragma unroll
+  for (int k = 0; k < 18; ++k) b1[k] = b2[k] = 0;
+  int c[4] = {0, 0, 0, 0};
+  int ph = 1;
+  if (active) {
+    cb_coords(g, i, p, c);
+    const int j = cb_neighbour(g, i, c, mu, true, ph);
+    const char* psi_x = psi + p * half_bytes + (size_t)i * site_bytes;
+    const char* chi_x = chi + p * half_bytes + (size_t)i * site_bytes;
+    const char* psi_f = psi + (1 - p) * half_bytes + (size_t)j * site_bytes;
+    const char* chi_f = chi + (1 - p) * half_bytes + (size_t)j * site_bytes;
+    for (int s = lane; s < Ls; s += nsg) {
+      R v[24], ha[12], hb[12];
+      load_spinor<P>(psi_f, s, Ls, v);
+      project<-1>(mu, v, ha);
+      load_spinor<P>(chi_x, s, Ls, v);
+      project<-1>(mu, v, hb);
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {  // b1[a][b] += ha[h][a] conj(hb[h][b])
+            const R xr = ha[(h * 3 + a) * 2], xi = ha[(h * 3 + a) * 2 + 1];
+            const R yr = hb[(h * 3 + b) * 2], yi = hb[(h * 3 + b) * 2 + 1];
+            b1[(a * 3 + b) * 2] += xr * yr + xi * yi;
+            b1[(a * 3 + b) * 2 + 1] += xi * yr - xr * yi;
+          }
+      load_spinor<P>(psi_x, s, Ls, v);
+      project<+1>(mu, v, ha);
+      load_spinor<P>(chi_f, s, Ls, v);
+      project<+1>(mu, v, hb);
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            const R xr = ha[(h * 3 + a) * 2], xi = ha[(h * 3 + a) * 2 + 1];
+            const R yr = hb[(h * 3 + b) * 2], yi = hb[(h * 3 + b) * 2 + 1];
+            b2[(a * 3 + b) * 2] += xr * yr + xi * yi;
+            b2[(a * 3 + b) * 2 + 1] += xi * yr - xr * yi;
+          }
+    }
+  }
+  // combine the nsg lanes of this link in FP64
+  double B1[18], B2[18];
+#pragma unroll
+  for (int k = 0; k < 18; ++k) {
+    B1[k] = (double)b1[k];
+    B2[k] = (double)b2[k];
+  }
+  for (int off = nsg / 2; off > 0; off >>= 1) {
+#pragma unroll
+    for (int k = 0; k < 18; ++k) {
+      B1[k] += __shfl_xor_sync(0xffffffffu, B1[k], off, nsg);
+      B2[k] += __shfl_xor_sync(0xffffffffu, B2[k], off, nsg);
+    }
+  }
+  if (!active || lane != 0) return;
+
+  R ur[18];
+  load_link<P, C12>((p ? Uo : Ue) + ((size_t)i * 4 + mu) * LB, ur);
+  double u[18];
+#pragma unroll
+  for (int k = 0; k < 18; ++k) u[k] = (double)ur[k];
+  const double phd = (double)ph;
+  const long lex = c[0] + (long)g.L[0] * (c[1] + (long)g.L[1] * (c[2] + (long)g.L[2] * c[3]));
+  double* Fo = F ? F + (lex * 4 + mu) * 18 : nullptr;
+  double* Go = G ? G + (lex * 4 + mu) * 18 : nullptr;
+  if (Go) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {  // G[a][b] = -phase (conj(B1[b][a]) + B2[a][b])
+        Go[(a * 3 + b) * 2] = -phd * (B1[(b * 3 + a) * 2] + B2[(a * 3 + b) * 2]);
+        Go[(a * 3 + b) * 2 + 1] = -phd * (-B1[(b * 3 + a) * 2 + 1] + B2[(a * 3 + b) * 2 + 1]);
+      }
+  }
+  if (Fo) {
+    double Y[18];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {  // Y = phase (-U B1 + B2 U^+)
+        double yr = 0, yi = 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const double ar = u[(a * 3 + k) * 2], ai = u[(a * 3 + k) * 2 + 1];
+          const double br = B1[(k * 3 + b) * 2], bi = B1[(k * 3 + b) * 2 + 1];
+          yr -= ar * br - ai * bi;
+          yi -= ar * bi + ai * br;
+          const double cr = B2[(a * 3 + k) * 2], ci = B2[(a * 3 + k) * 2 + 1];
+          const double dr = u[(b * 3 + k) * 2], di = -u[(b * 3 + k) * 2 + 1];  // (U^+)[k][b] = conj(U[b][k])
+          yr += cr * dr - ci * di;
+          yi += cr * di + ci * dr;
+        }
+        Y[(a * 3 + b) * 2] = phd * yr;
+        Y[(a * 3 + b) * 2 + 1] = phd * yi;
+      }
+    // F = -TA(Y): TA(Y)[a][b] = (Y[a][b] - conj(Y[b][a]))/2 - delta_ab tr(Y - Y^+)/6
+    const double trim = (Y[1] + Y[9] + Y[17]);  // Im tr Y; tr(Y - Y^+) = 2 i Im tr Y
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        double tr_ = 0.5 * (Y[(a * 3 + b) * 2] - Y[(b * 3 + a) * 2]);
+        double ti_ = 0.5 * (Y[(a * 3 + b) * 2 + 1] + Y[(b * 3 + a) * 2 + 1]);
+        if (a == b) ti_ -= trim / 3.0;
+        Fo[(a * 3 + b) * 2] = -tr_;
+        Fo[(a * 3 + b) * 2 + 1] = -ti_;
+      }
+  }
+}
+
+cudaError_t launch_force(int prec, bool c12, const Geom& g, const void* psi, const void* chi, const void* Ue,
+                         const void* Uo, double* F, double* G, cudaStream_t st) {
+  int nsg = 1;
+  while (nsg * 2 <= g.Ls && nsg < 8) nsg *= 2;
+  const int threads = 256;
+  const long links = 8L * g.N4h;
+  const int links_per_cta = threads / nsg;
+  const int blocks = (int)((links + links_per_cta - 1) / links_per_cta);
+  const char* ps = static_cast<const char*>(psi);
+  const char* ch = static_cast<const char*>(chi);
+  const char* e = static_cast<const char*>(Ue);
+  const char* o = static_cast<const char*>(Uo);
+#define FK(P_)                                                                         \
+  if (c12)                                                                             \
+    k_force<P_, true><<<blocks, threads, 0, st>>>(g, ps, ch, e, o, F, G, nsg);         \
+  else                                                                                 \
+    k_force<P_, false><<<blocks, threads, 0, st>>>(g, ps, ch, e, o, F, G, nsg);
+  switch (prec) {
+    case P64: FK(P64) break;
+    case P32: FK(P32) break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef FK
+  return cudaGetLastError();
+}
+
+}  // namespace gdwf

@@ -1,0 +1,599 @@
+// Site-local kernels: layout and precision conversion, standalone Mooee / Mooee^-1,
+// FP64-accumulated reductions and CG vector updates. All are bandwidth-bound passes over the
+// device field layout described in dwf_common.cuh.
+//
+// Elementwise kernels walk a field in units of 8 reals: unit (site, g, s) is reals 8g..8g+7 of
+// slice s of a site block. Consecutive threads take consecutive s, so every precision's
+// 16-byte vectors are read and written contiguously, and fields of different precisions (whose
+// chunks hold 2, 4 or 8 reals) can be combined in one pass.
+#include "dhop_kernel.cuh"
+#include "site_ops.cuh"
+
+namespace gdwf {
+
+template <int P>
+using RT = typename Store<P>::R;
+
+template <int P>
+__device__ __forceinline__ const char* site_ptr(const void* base, long site, int Ls) {
+  return static_cast<const char*>(base) + (size_t)site * Ls * 24 * sizeof(typename Store<P>::T);
+}
+
+template <int P, bool COHERENT>
+__device__ __forceinline__ void ld8(const void* base, long site, int g, int s, int Ls, RT<P>* o) {
+  constexpr int VEC = Store<P>::VEC;
+  constexpr int NV = 8 / VEC;
+  const char* sb = site_ptr<P>(base, site, Ls);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const char* q = sb + ((size_t)(g * NV + v) * Ls + s) * 16;
+    if (COHERENT)
+      ld16c<P>(q, o + v * VEC);
+    else
+      ld16<P>(q, o + v * VEC);
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void st8(void* base, long site, int g, int s, int Ls, const RT<P>* o) {
+  constexpr int VEC = Store<P>::VEC;
+  constexpr int NV = 8 / VEC;
+  char* sb = const_cast<char*>(site_ptr<P>(base, site, Ls));
+#pragma unroll
+  for (int v = 0; v < NV; ++v) st16<P>(sb + ((size_t)(g * NV + v) * Ls + s) * 16, o + v * VEC);
+}
+
+template <int P>
+__device__ __forceinline__ void st8d(void* base, long site, int g, int s, int Ls, const double* o) {
+  constexpr int VEC = Store<P>::VEC;
+  constexpr int NV = 8 / VEC;
+  char* sb = const_cast<char*>(site_ptr<P>(base, site, Ls));
+#pragma unroll
+  for (int v = 0; v < NV; ++v) st16d<P>(sb + ((size_t)(g * NV + v) * Ls + s) * 16, o + v * VEC);
+}
+
+__device__ __forceinline__ void unit_coords(long u, int Ls, long& site, int& g, int& s) {
+  const long rem = u / Ls;
+  s = (int)(u - rem * Ls);
+  site = rem / 3;
+  g = (int)(rem - site * 3);
+}
+
+static inline int grid_for(long n, int threads) {
+  long b = (n + threads - 1) / threads;
+  return (int)(b < 1 ? 1 : b);
+}
+
+// ---------------------------------------------------------------- block reduction
+
+template <int N>
+__device__ __forceinline__ void block_sum(double (&v)[N], double* partials, int nblocks) {
+  __shared__ double red[N][RED_THREADS / 32];
+#pragma unroll
+  for (int k = 0; k < N; ++k)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < N; ++k) red[k][warp] = v[k];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      double t = lane < RED_THREADS / 32 ? red[k][lane] : 0.0;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+      if (lane == 0) partials[k * nblocks + blockIdx.x] = t;
+    }
+  }
+}
+
+// Second pass: one CTA sums the RED_BLOCKS partials in a fixed order.
+__global__ void __launch_bounds__(RED_THREADS) k_finalize(const double* partials, int ncomp, double* scal, int kind,
+                                                         int dst) {
+  __shared__ double red[2][RED_THREADS];
+  for (int k = 0; k < ncomp; ++k) {
+    double t = 0;
+    for (int i = threadIdx.x; i < RED_BLOCKS; i += RED_THREADS) t += partials[k * RED_BLOCKS + i];
+    red[k][threadIdx.x] = t;
+  }
+  __syncthreads();
+  for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int k = 0; k < ncomp; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double tot = red[0][0];
+    if (kind == FIN_STORE) {
+      scal[dst] = tot;
+      if (ncomp > 1) scal[dst + 1] = red[1][0];
+    } else if (kind == FIN_ALPHA) {
+      scal[S_PAP] = tot;
+      scal[S_ALPHA] = scal[S_RR] / tot;
+    } else if (kind == FIN_BETA) {
+      scal[S_RRNEW] = tot;
+      scal[S_BETA] = scal[S_PSCALE] * tot / scal[S_RR];
+      scal[S_RR] = tot;
+      scal[S_PSCALE] = 1.0;
+    }
+  }
+}
+
+static cudaError_t finalize(const double* partials, int ncomp, double* scal, int kind, int dst, cudaStream_t st) {
+  k_finalize<<<1, RED_THREADS, 0, st>>>(partials, ncomp, scal, kind, dst);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- pack / unpack
+
+template <int P>
+__global__ void k_pack_spinor(Geom g, double* canon, char* field, int parity0, int nparity, bool unpack) {
+  using R = RT<P>;
+  constexpr int VEC = Store<P>::VEC, NCH = 24 / VEC;
+  const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  const int Ls = g.Ls;
+  const long total = (long)nparity * g.N4h * NCH * Ls;
+  if (tid >= total) return;
+  const long rem = tid / Ls;
+  const int s = (int)(tid - rem * Ls);
+  const long sitep = rem / NCH;
+  const int k = (int)(rem - sitep * NCH);
+  const int ph = (int)(sitep / g.N4h);
+  const int i = (int)(sitep - (long)ph * g.N4h);
+  int c[4];
+  cb_coords(g, i, parity0 + ph, c);
+  const long lex = c[0] + (long)g.L[0] * (c[1] + (long)g.L[1] * (c[2] + (long)g.L[2] * c[3]));
+  double* cp = canon + ((lex * Ls + s) * 24 + k * VEC);
+  char* fp = field + (size_t)sitep * Ls * 24 * sizeof(typename Store<P>::T) + ((size_t)k * Ls + s) * 16;
+  if (!unpack) {
+    double v[VEC];
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) v[j] = cp[j];
+    st16d<P>(fp, v);
+  } else {
+    R v[VEC];
+    ld16<P>(fp, v);
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) cp[j] = (double)v[j];
+  }
+}
+
+cudaError_t launch_pack_spinor(int prec, const Geom& g, const double* canon, void* field, int subset, bool unpack,
+                               cudaStream_t st) {
+  const int parity0 = subset == 2 ? 0 : subset;
+  const int nparity = subset == 2 ? 2 : 1;
+  const long total = (long)nparity * g.N4h * (24 / prec_vec(prec)) * g.Ls;
+  const int blocks = grid_for(total, 256);
+  double* c = const_cast<double*>(canon);
+  char* f = static_cast<char*>(field);
+  switch (prec) {
+    case P64: k_pack_spinor<P64><<<blocks, 256, 0, st>>>(g, c, f, parity0, nparity, unpack); break;
+    case P32: k_pack_spinor<P32><<<blocks, 256, 0, st>>>(g, c, f, parity0, nparity, unpack); break;
+    case P16: k_pack_spinor<P16><<<blocks, 256, 0, st>>>(g, c, f, parity0, nparity, unpack); break;
+    default: k_pack_spinor<PB16><<<blocks, 256, 0, st>>>(g, c, f, parity0, nparity, unpack); break;
+  }
+  return cudaGetLastError();
+}
+
+template <int P, bool C12>
+__global__ void k_pack_gauge(Geom g, const double* canon, char* Ue, char* Uo) {
+  using R = RT<P>;
+  constexpr int VEC = Store<P>::VEC;
+  constexpr int LB = link_bytes(sizeof(typename Store<P>::T), C12);
+  constexpr int NR = C12 ? 12 : 18;
+  constexpr int NV = LB / 16;
+  const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (tid >= 8L * g.N4h) return;
+  const int mu = (int)(tid & 3);
+  const long rem = tid >> 2;
+  const int p = rem >= g.N4h ? 1 : 0;
+  const int i = (int)(rem - (long)p * g.N4h);
+  int c[4];
+  cb_coords(g, i, p, c);
+  const long lex = c[0] + (long)g.L[0] * (c[1] + (long)g.L[1] * (c[2] + (long)g.L[2] * c[3]));
+  const double* u = canon + (lex * 4 + mu) * 18;
+  char* dst = (p ? Uo : Ue) + ((size_t)i * 4 + mu) * LB;
+  double buf[NV * VEC];
+#pragma unroll
+  for (int j = 0; j < NV * VEC; ++j) buf[j] = j < NR ? u[j] : 0.0;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) st16d<P>(dst + v * 16, buf + v * VEC);
+}
+
+cudaError_t launch_pack_gauge(int prec, bool c12, const Geom& g, const double* canon, void* Ue, void* Uo,
+                              cudaStream_t st) {
+  const int blocks = grid_for(8L * g.N4h, 256);
+  char* e = static_cast<char*>(Ue);
+  char* o = static_cast<char*>(Uo);
+#define PG(P_)                                                                   \
+  if (c12)                                                                       \
+    k_pack_gauge<P_, true><<<blocks, 256, 0, st>>>(g, canon, e, o);              \
+  else                                                                           \
+    k_pack_gauge<P_, false><<<blocks, 256, 0, st>>>(g, canon, e, o);
+  switch (prec) {
+    case P64: PG(P64) break;
+    case P32: PG(P32) break;
+    case P16: PG(P16) break;
+    default: PG(PB16) break;
+  }
+#undef PG
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- precision conversion
+
+template <int PS, int PD>
+__global__ void k_convert(const void* src, void* dst, long nsites, int Ls, const double* scale_dev, double scale) {
+  using RS = RT<PS>;
+  using RD = RT<PD>;
+  const double sc = scale_dev ? *scale_dev : scale;
+  const long units = nsites * 3 * Ls;
+  for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < units; u += (long)gridDim.x * blockDim.x) {
+    long site;
+    int g, s;
+    unit_coords(u, Ls, site, g, s);
+    RS a[8];
+    ld8<PS, false>(src, site, g, s, Ls, a);
+    if constexpr (PS == P64 || PD == P64) {
+      double b[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) b[j] = (double)a[j] * sc;
+      st8d<PD>(dst, site, g, s, Ls, b);
+    } else {
+      RD b[8];
+      const float f = (float)sc;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) b[j] = (RD)((float)a[j] * f);
+      st8<PD>(dst, site, g, s, Ls, b);
+    }
+  }
+}
+
+cudaError_t launch_convert(int psrc, int pdst, const void* src, void* dst, long nsites, int Ls, const double* scale_dev,
+                           double scale, cudaStream_t st) {
+  const int blocks = grid_for(nsites * 3 * Ls, 256);
+#define CV(A, B) k_convert<A, B><<<blocks, 256, 0, st>>>(src, dst, nsites, Ls, scale_dev, scale)
+#define CVROW(A)            \
+  switch (pdst) {           \
+    case P64: CV(A, P64); break;  \
+    case P32: CV(A, P32); break;  \
+    case P16: CV(A, P16); break;  \
+    default: CV(A, PB16); break;  \
+  }
+  switch (psrc) {
+    case P64: CVROW(P64) break;
+    case P32: CVROW(P32) break;
+    case P16: CVROW(P16) break;
+    default: CVROW(PB16) break;
+  }
+#undef CVROW
+#undef CV
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- standalone Mooee / Mooee^-1
+
+// One CTA holds `spc` whole sites in shared memory (FP32 or FP64 arithmetic): load, apply the
+// fifth-dimension operator, store. in and out may be the same buffer.
+template <int P>
+__global__ void __launch_bounds__(256) k_mooee(const void* in, void* out, long nsites, int Ls, int spc, bool dag,
+                                               bool inverse, double d5, double mass, double inv_d5, double inv_den) {
+  using R = RT<P>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* sm = reinterpret_cast<R*>(smem_raw);
+  const long site0 = (long)blockIdx.x * spc;
+  const int ns = (int)min((long)spc, nsites - site0);
+  const int units = ns * 3 * Ls;
+  for (int u = threadIdx.x; u < units; u += blockDim.x) {
+    const int rem = u / Ls;
+    const int s = u - rem * Ls;
+    const int sl = rem / 3;
+    const int g = rem - sl * 3;
+    R v[8];
+    ld8<P, true>(in, site0 + sl, g, s, Ls, v);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) sm[((size_t)sl * Ls + s) * 24 + 8 * g + j] = v[j];
+  }
+  __syncthreads();
+  if (inverse) {
+    for (int task = threadIdx.x; task < ns * 24; task += blockDim.x) {
+      const int sl = task / 24;
+      const int r = task - sl * 24;
+      const bool upper = r < 12;
+      mooee_inv_line<R>(sm + (size_t)sl * Ls * 24 + r, Ls, dag ? !upper : upper, R(mass), R(inv_d5), R(inv_den));
+    }
+    __syncthreads();
+    for (int u = threadIdx.x; u < units; u += blockDim.x) {
+      const int rem = u / Ls;
+      const int s = u - rem * Ls;
+      const int sl = rem / 3;
+      const int g = rem - sl * 3;
+      st8<P>(out, site0 + sl, g, s, Ls, sm + ((size_t)sl * Ls + s) * 24 + 8 * g);
+    }
+    return;
+  }
+  for (int u = threadIdx.x; u < units; u += blockDim.x) {
+    const int rem = u / Ls;
+    const int s = u - rem * Ls;
+    const int sl = rem / 3;
+    const int g = rem - sl * 3;
+    const int sm1 = s > 0 ? s - 1 : Ls - 1, sp1 = s < Ls - 1 ? s + 1 : 0;
+    const R cm = s > 0 ? R(-1) : R(mass), cp = s < Ls - 1 ? R(-1) : R(mass);
+    const int s_up = dag ? sp1 : sm1, s_lo = dag ? sm1 : sp1;
+    const R c_up = dag ? cp : cm, c_lo = dag ? cm : cp;
+    const R* base = sm + (size_t)sl * Ls * 24;
+    R o[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int r = 8 * g + j;
+      const bool upper = r < 12;
+      o[j] = R(d5) * base[s * 24 + r] + (upper ? c_up * base[s_up * 24 + r] : c_lo * base[s_lo * 24 + r]);
+    }
+    st8<P>(out, site0 + sl, g, s, Ls, o);
+  }
+}
+
+cudaError_t launch_mooee(int prec, const void* in, void* out, long nsites, int Ls, bool dag, bool inverse, double d5,
+                         double mass, double inv_d5, double inv_den, cudaStream_t st) {
+  const size_t rbytes = prec == P64 ? 8 : 4;
+  const size_t site_smem = (size_t)Ls * 24 * rbytes;
+  int spc = (int)((48 * 1024) / site_smem);
+  if (spc > 64) spc = 64;
+  if (spc < 1) return cudaErrorInvalidValue;
+  const size_t smem = spc * site_smem;
+  const int blocks = grid_for(nsites, spc);
+#define MO(P_) k_mooee<P_><<<blocks, 256, smem, st>>>(in, out, nsites, Ls, spc, dag, inverse, d5, mass, inv_d5, inv_den)
+  switch (prec) {
+    case P64: MO(P64); break;
+    case P32: MO(P32); break;
+    case P16: MO(P16); break;
+    default: MO(PB16); break;
+  }
+#undef MO
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- reductions
+
+// Sum over 8 reals of a unit: |a|^2, or the complex a^+ b. Lower precisions form the 8-term
+// partial in FP32 and add it to the FP64 accumulator; FP64 data is accumulated in FP64.
+template <int P, bool INNER>
+__global__ void __launch_bounds__(RED_THREADS) k_reduce(const void* a, const void* b, long nsites, int Ls,
+                                                        double* partials) {
+  using R = RT<P>;
+  double acc[2] = {0.0, 0.0};
+  const long units = nsites * 3 * Ls;
+  for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < units; u += (long)gridDim.x * blockDim.x) {
+    long site;
+    int g, s;
+    unit_coords(u, Ls, site, g, s);
+    R x[8];
+    ld8<P, false>(a, site, g, s, Ls, x);
+    if (INNER) {
+      R y[8];
+      ld8<P, false>(b, site, g, s, Ls, y);
+      R re = 0, im = 0;
+#pragma unroll
+      for (int j = 0; j < 8; j += 2) {
+        re += x[j] * y[j] + x[j + 1] * y[j + 1];
+        im += x[j] * y[j + 1] - x[j + 1] * y[j];
+      }
+      acc[0] += (double)re;
+      acc[1] += (double)im;
+    } else {
+      R t = 0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) t += x[j] * x[j];
+      acc[0] += (double)t;
+    }
+  }
+  if (INNER) {
+    block_sum<2>(acc, partials, RED_BLOCKS);
+  } else {
+    double v[1] = {acc[0]};
+    block_sum<1>(v, partials, RED_BLOCKS);
+  }
+}
+
+cudaError_t launch_reduce(int prec, const void* a, const void* b, long nsites, int Ls, double* partials, double* scal,
+                          int kind, int dst, cudaStream_t st) {
+  const bool inner = b != nullptr;
+#define RD(P_)                                                                              \
+  if (inner)                                                                                \
+    k_reduce<P_, true><<<RED_BLOCKS, RED_THREADS, 0, st>>>(a, b, nsites, Ls, partials);     \
+  else                                                                                      \
+    k_reduce<P_, false><<<RED_BLOCKS, RED_THREADS, 0, st>>>(a, b, nsites, Ls, partials);
+  switch (prec) {
+    case P64: RD(P64) break;
+    case P32: RD(P32) break;
+    case P16: RD(P16) break;
+    default: RD(PB16) break;
+  }
+#undef RD
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return finalize(partials, inner ? 2 : 1, scal, kind, dst, st);
+}
+
+// ---------------------------------------------------------------- CG updates
+
+template <int PX, int PP>
+__global__ void __launch_bounds__(RED_THREADS) k_cg_xr(void* x, void* r, const void* p, const void* Ap, long nsites,
+                                                       int Ls, const double* scal, double* partials) {
+  using RX = RT<PX>;
+  using RP = RT<PP>;
+  const RX alpha = (RX)scal[S_ALPHA];
+  double acc = 0.0;
+  const long units = nsites * 3 * Ls;
+  for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < units; u += (long)gridDim.x * blockDim.x) {
+    long site;
+    int g, s;
+    unit_coords(u, Ls, site, g, s);
+    RX xv[8], rv[8];
+    RP pv[8], av[8];
+    ld8<PX, true>(x, site, g, s, Ls, xv);
+    ld8<PX, true>(r, site, g, s, Ls, rv);
+    ld8<PP, false>(p, site, g, s, Ls, pv);
+    ld8<PP, false>(Ap, site, g, s, Ls, av);
+    RX t = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      xv[j] += alpha * (RX)pv[j];
+      rv[j] -= alpha * (RX)av[j];
+      t += rv[j] * rv[j];
+    }
+    st8<PX>(x, site, g, s, Ls, xv);
+    st8<PX>(r, site, g, s, Ls, rv);
+    acc += (double)t;
+  }
+  double v[1] = {acc};
+  block_sum<1>(v, partials, RED_BLOCKS);
+}
+
+template <int PX, int PP>
+__global__ void k_cg_p(const void* r, void* p, long nsites, int Ls, const double* scal) {
+  using RX = RT<PX>;
+  using RP = RT<PP>;
+  const RX beta = (RX)scal[S_BETA];
+  const long units = nsites * 3 * Ls;
+  for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < units; u += (long)gridDim.x * blockDim.x) {
+    long site;
+    int g, s;
+    unit_coords(u, Ls, site, g, s);
+    RX rv[8];
+    RP pv[8];
+    ld8<PX, false>(r, site, g, s, Ls, rv);
+    ld8<PP, true>(p, site, g, s, Ls, pv);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) pv[j] = (RP)(rv[j] + beta * (RX)pv[j]);
+    st8<PP>(p, site, g, s, Ls, pv);
+  }
+}
+
+#define CG_PAIRS(M) \
+  M(P64, P64)       \
+  M(P32, P32)       \
+  M(P32, P16)       \
+  M(P32, PB16)
+
+cudaError_t launch_cg_xr(int px, int pp, void* x, void* r, const void* p, const void* Ap, long nsites, int Ls,
+                         double* partials, double* scal, cudaStream_t st) {
+#define XR(A, B)                                                                                  \
+  if (px == A && pp == B) {                                                                       \
+    k_cg_xr<A, B><<<RED_BLOCKS, RED_THREADS, 0, st>>>(x, r, p, Ap, nsites, Ls, scal, partials);  \
+    cudaError_t e = cudaGetLastError();                                                           \
+    if (e != cudaSuccess) return e;                                                               \
+    return finalize(partials, 1, scal, FIN_BETA, 0, st);                                          \
+  }
+  CG_PAIRS(XR)
+#undef XR
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_cg_p(int px, int pp, const void* r, void* p, long nsites, int Ls, const double* scal,
+                        cudaStream_t st) {
+  const int blocks = grid_for(nsites * 3 * Ls, 256);
+#define PU(A, B)                                                              \
+  if (px == A && pp == B) {                                                   \
+    k_cg_p<A, B><<<blocks, 256, 0, st>>>(r, p, nsites, Ls, scal);             \
+    return cudaGetLastError();                                                \
+  }
+  CG_PAIRS(PU)
+#undef PU
+  return cudaErrorInvalidValue;
+}
+
+__global__ void __launch_bounds__(RED_THREADS) k_residual64(const void* b, const void* Ax, void* r, long nsites, int Ls,
+                                                            double* partials) {
+  double acc = 0.0;
+  const long units = nsites * 3 * Ls;
+  for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < units; u += (long)gridDim.x * blockDim.x) {
+    long site;
+    int g, s;
+    unit_coords(u, Ls, site, g, s);
+    double bv[8], av[8];
+    ld8<P64, false>(b, site, g, s, Ls, bv);
+    ld8<P64, false>(Ax, site, g, s, Ls, av);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      bv[j] -= av[j];
+      acc += bv[j] * bv[j];
+    }
+    st8<P64>(r, site, g, s, Ls, bv);
+  }
+  double v[1] = {acc};
+  block_sum<1>(v, partials, RED_BLOCKS);
+}
+
+cudaError_t launch_residual64(const void* b, const void* Ax, void* r, long nsites, int Ls, double* partials,
+                              double* scal, int dst, cudaStream_t st) {
+  k_residual64<<<RED_BLOCKS, RED_THREADS, 0, st>>>(b, Ax, r, nsites, Ls, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return finalize(partials, 1, scal, FIN_STORE, dst, st);
+}
+
+template <int PY>
+__global__ void k_accum_zero(void* x, void* y, long nsites, int Ls, const double* c_dev) {
+  using RY = RT<PY>;
+  const double c = *c_dev;
+  const long units = nsites * 3 * Ls;
+  for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < units; u += (long)gridDim.x * blockDim.x) {
+    long site;
+    int g, s;
+    unit_coords(u, Ls, site, g, s);
+    double xv[8];
+    RY yv[8];
+    ld8<P64, true>(x, site, g, s, Ls, xv);
+    ld8<PY, true>(y, site, g, s, Ls, yv);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      xv[j] += c * (double)yv[j];
+      yv[j] = RY(0);
+    }
+    st8<P64>(x, site, g, s, Ls, xv);
+    st8<PY>(y, site, g, s, Ls, yv);
+  }
+}
+
+cudaError_t launch_accum_zero(int py, void* x, void* y, long nsites, int Ls, const double* c_dev, cudaStream_t st) {
+  const int blocks = grid_for(nsites * 3 * Ls, 256);
+  switch (py) {
+    case P64: k_accum_zero<P64><<<blocks, 256, 0, st>>>(x, y, nsites, Ls, c_dev); break;
+    case P32: k_accum_zero<P32><<<blocks, 256, 0, st>>>(x, y, nsites, Ls, c_dev); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <int P>
+__global__ void k_axpby(double a, const void* x, double b, void* y, long nsites, int Ls) {
+  using R = RT<P>;
+  const long units = nsites * 3 * Ls;
+  for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < units; u += (long)gridDim.x * blockDim.x) {
+    long site;
+    int g, s;
+    unit_coords(u, Ls, site, g, s);
+    R xv[8], yv[8];
+    ld8<P, true>(x, site, g, s, Ls, xv);
+    ld8<P, true>(y, site, g, s, Ls, yv);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) yv[j] = R(a) * xv[j] + R(b) * yv[j];
+    st8<P>(y, site, g, s, Ls, yv);
+  }
+}
+
+cudaError_t launch_axpby(int p, double a, const void* x, double b, void* y, long nsites, int Ls, cudaStream_t st) {
+  const int blocks = grid_for(nsites * 3 * Ls, 256);
+  switch (p) {
+    case P64: k_axpby<P64><<<blocks, 256, 0, st>>>(a, x, b, y, nsites, Ls); break;
+    case P32: k_axpby<P32><<<blocks, 256, 0, st>>>(a, x, b, y, nsites, Ls); break;
+    case P16: k_axpby<P16><<<blocks, 256, 0, st>>>(a, x, b, y, nsites, Ls); break;
+    default: k_axpby<PB16><<<blocks, 256, 0, st>>>(a, x, b, y, nsites, Ls); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace gdwf

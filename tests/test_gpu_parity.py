@@ -1,0 +1,321 @@
+"""Parity of the CUDA library (through the C ABI) with the FP64 oracle, element by element.
+
+Tolerances are relative L2 norms over the whole field, |y_gpu - y_ref| / |y_ref|:
+  FP64 1e-12; FP32 1e-5 (both from the operator's specification);
+  FP16 / BF16 storage with FP32 arithmetic, against the oracle applied to the same rounded
+  inputs: the output is rounded once to the storage format (unit roundoff 2^-11 / 2^-8) after
+  FP32 arithmetic, so 2e-3 (FP16) and 1.6e-2 (BF16) bound it with margin; against the exact
+  inputs the error is reported and bounded loosely (input rounding of 24 + 18 reals per hop).
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2203_06777_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+BC = (1, 1, 1, -1)
+M5, MASS = 1.8, 0.01
+TOL = {0: 1e-12, 1: 1e-5, 2: 2e-3, 3: 1.6e-2}
+
+
+@pytest.fixture(scope="module")
+def dwf():
+    from paper_2203_06777_gb300 import dwf as mod
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    mod.load()
+    return mod
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def parity_fields(oracle, dims, psi):
+    odd = oracle.parity_mask(dims)[..., None, None, None]
+    return psi * ~odd, psi * odd
+
+
+def round_spinor(x, prec):
+    """The canonical field as the library stores it in `prec` (round to nearest), back in FP64."""
+    if prec == 0:
+        return x
+    if prec == 1:
+        f = lambda a: a.astype(np.float32).astype(np.float64)
+    elif prec == 2:
+        f = lambda a: a.astype(np.float16).astype(np.float64)
+    else:  # bfloat16: 8 significant bits, round to nearest even, straight from FP64
+        def f(a):
+            m, e = np.frexp(a)
+            return np.ldexp(np.rint(m * 256.0) / 256.0, e)
+    return f(x.real) + 1j * f(x.imag)
+
+
+def make(dwf, dims, Ls, seed, eps=None, compress12=False, bc=BC, mass=MASS):
+    U = synth.random_gauge(dims, seed=seed, eps=eps)
+    op = dwf.GridDWF(dims, Ls, M5, mass, bc=bc, compress12=compress12)
+    op.set_gauge(dev(U))
+    return op, U
+
+
+# ---------------------------------------------------------------- layout
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+def test_pack_unpack_roundtrip(dwf, oracle_lib, prec):
+    dims, Ls = (4, 2, 6, 4), 3
+    op, _ = make(dwf, dims, Ls, 1)
+    psi = synth.random_spinor(dims, Ls, seed=2)
+    f = op.pack(dev(psi), prec, dwf.FULL)
+    back = host(op.unpack(f))
+    assert np.array_equal(back, round_spinor(psi, prec))
+    for sub in (dwf.EVEN, dwf.ODD):
+        h = op.pack(dev(psi), prec, sub)
+        b = host(op.unpack(h, subset=sub))
+        mask = oracle_lib.parity_mask(dims)
+        m = mask if sub == dwf.ODD else ~mask
+        assert np.array_equal(b[m], round_spinor(psi, prec)[m])
+        assert np.all(b[~m] == 0)
+
+
+# ---------------------------------------------------------------- Dhop
+
+DHOP_CASES = [((4, 4, 4, 4), 8, None), ((4, 4, 4, 4), 16, 0.3), ((2, 4, 6, 4), 3, None), ((6, 2, 4, 2), 12, None),
+              ((4, 6, 2, 4), 1, None), ((2, 2, 2, 2), 2, None), ((8, 4, 4, 6), 4, 0.5)]
+
+
+@pytest.mark.parametrize("dims,Ls,eps", DHOP_CASES)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_dhop_parity(dwf, oracle_lib, dims, Ls, eps, prec):
+    op, U = make(dwf, dims, Ls, 11, eps=eps)
+    psi = synth.random_spinor(dims, Ls, seed=12)
+    f = op.pack(dev(psi), prec, dwf.FULL)
+    psi_r = round_spinor(psi, prec)
+    U_r = round_spinor(U, prec)
+    for dag in (False, True):
+        ref = oracle_lib.dhop(dims, Ls, BC, U_r, psi_r, dag=dag)
+        out = host(op.unpack(op.dhop(f, dwf.FULL, dag=dag)))
+        assert rel(out, ref) < TOL[prec], (dag, rel(out, ref))
+        # half-lattice forms: EO reads the odd half, OE the even half
+        pe, po = parity_fields(oracle_lib, dims, psi)
+        fo = op.pack(dev(po), prec, dwf.ODD)
+        fe = op.pack(dev(pe), prec, dwf.EVEN)
+        eo = host(op.unpack(op.dhop(fo, dwf.EVEN, dag=dag), subset=dwf.EVEN))
+        oe = host(op.unpack(op.dhop(fe, dwf.ODD, dag=dag), subset=dwf.ODD))
+        mask = oracle_lib.parity_mask(dims)
+        assert rel(eo[~mask], ref[~mask]) < TOL[prec]
+        assert rel(oe[mask], ref[mask]) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [2, 3])
+@pytest.mark.parametrize("dims,Ls", [((4, 4, 4, 4), 8), ((2, 4, 6, 4), 3), ((4, 4, 2, 2), 16)])
+def test_dhop_low_precision_storage(dwf, oracle_lib, prec, dims, Ls):
+    op, U = make(dwf, dims, Ls, 21, eps=0.3)
+    psi = synth.random_spinor(dims, Ls, seed=22)
+    f = op.pack(dev(psi), prec, dwf.FULL)
+    for dag in (False, True):
+        out = host(op.unpack(op.dhop(f, dwf.FULL, dag=dag)))
+        ref_same_inputs = oracle_lib.dhop(dims, Ls, BC, round_spinor(U, prec), round_spinor(psi, prec), dag=dag)
+        assert rel(out, ref_same_inputs) < TOL[prec]
+        ref_exact = oracle_lib.dhop(dims, Ls, BC, U, psi, dag=dag)
+        assert rel(out, ref_exact) < 4 * TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_dhop_compressed_links(dwf, oracle_lib, prec):
+    dims, Ls = (4, 4, 6, 4), 6
+    op, U = make(dwf, dims, Ls, 31, compress12=True)
+    psi = synth.random_spinor(dims, Ls, seed=32)
+    f = op.pack(dev(psi), prec, dwf.FULL)
+    out = host(op.unpack(op.dhop(f, dwf.FULL)))
+    ref = oracle_lib.dhop(dims, Ls, BC, U, psi)
+    tol = {0: 1e-12, 1: 1e-5, 2: 4 * TOL[2]}[prec]
+    assert rel(out, ref) < tol
+
+
+def test_dhop_boundary_conditions(dwf, oracle_lib):
+    dims, Ls = (4, 2, 4, 6), 4
+    for bc in [(1, 1, 1, 1), (-1, 1, 1, -1), (-1, -1, -1, -1), (1, -1, 1, 1)]:
+        op, U = make(dwf, dims, Ls, 41, bc=bc)
+        psi = synth.random_spinor(dims, Ls, seed=42)
+        f = op.pack(dev(psi), 0, dwf.FULL)
+        assert rel(host(op.unpack(op.dhop(f, dwf.FULL))), oracle_lib.dhop(dims, Ls, bc, U, psi)) < 1e-12
+
+
+# ---------------------------------------------------------------- fifth dimension, M, Schur
+
+
+@pytest.mark.parametrize("Ls", [1, 2, 7, 8, 16])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_mooee_family(dwf, oracle_lib, Ls, prec):
+    dims = (4, 2, 2, 4)
+    op, _ = make(dwf, dims, Ls, 51)
+    psi = synth.random_spinor(dims, Ls, seed=52)
+    f = op.pack(dev(psi), prec, dwf.FULL)
+    psi_r = round_spinor(psi, prec)
+    for dag in (False, True):
+        for inv in (False, True):
+            out = host(op.unpack(op.mooee(f, dag=dag, inverse=inv)))
+            ref = oracle_lib.mooee(dims, Ls, M5, MASS, psi_r, dag=dag, inverse=inv)
+            assert rel(out, ref) < TOL[prec], (dag, inv)
+    g = f.clone()
+    op.mooee(g, inverse=True, out=g)  # in place
+    assert rel(host(op.unpack(g)), oracle_lib.mooee(dims, Ls, M5, MASS, psi_r, inverse=True)) < TOL[prec]
+
+
+@pytest.mark.parametrize("dims,Ls", [((4, 4, 4, 4), 8), ((2, 4, 6, 4), 5), ((6, 4, 2, 2), 12)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_m_mpc_mdagm(dwf, oracle_lib, dims, Ls, prec):
+    op, U = make(dwf, dims, Ls, 61)
+    psi = synth.random_spinor(dims, Ls, seed=62)
+    psi_r, U_r = round_spinor(psi, prec), round_spinor(U, prec)
+    f = op.pack(dev(psi), prec, dwf.FULL)
+    for dag in (False, True):
+        out = host(op.unpack(op.m(f, dag=dag)))
+        assert rel(out, oracle_lib.m(dims, Ls, M5, MASS, BC, U_r, psi_r, dag=dag)) < TOL[prec]
+    _, po = parity_fields(oracle_lib, dims, psi_r)
+    fo = op.pack(dev(po), prec, dwf.ODD)
+    mask = oracle_lib.parity_mask(dims)
+    for dag in (False, True):
+        out = host(op.unpack(op.mpc(fo, dag=dag), subset=dwf.ODD))
+        ref = oracle_lib.mpc(dims, Ls, M5, MASS, BC, U_r, po, dag=dag)
+        assert rel(out[mask], ref[mask]) < 4 * TOL[prec]
+    out = host(op.unpack(op.mdagm(fo), subset=dwf.ODD))
+    ref = oracle_lib.mdagm(dims, Ls, M5, MASS, BC, U_r, po)
+    assert rel(out[mask], ref[mask]) < 8 * TOL[prec]
+
+
+def test_mdagm_low_precision(dwf, oracle_lib):
+    dims, Ls = (4, 4, 4, 4), 8
+    for prec in (2, 3):
+        op, U = make(dwf, dims, Ls, 71, eps=0.3)
+        psi = synth.random_spinor(dims, Ls, seed=72)
+        _, po = parity_fields(oracle_lib, dims, psi)
+        fo = op.pack(dev(po), prec, dwf.ODD)
+        out = host(op.unpack(op.mdagm(fo), subset=dwf.ODD))
+        ref = oracle_lib.mdagm(dims, Ls, M5, MASS, BC, U, po)
+        mask = oracle_lib.parity_mask(dims)
+        assert rel(out[mask], ref[mask]) < 8 * TOL[prec]
+
+
+# ---------------------------------------------------------------- reductions
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+def test_norm_inner(dwf, prec):
+    dims, Ls = (4, 4, 2, 6), 5
+    op, _ = make(dwf, dims, Ls, 81)
+    a = synth.random_spinor(dims, Ls, seed=82)
+    b = synth.random_spinor(dims, Ls, seed=83)
+    fa, fb = op.pack(dev(a), prec, dwf.FULL), op.pack(dev(b), prec, dwf.FULL)
+    ar, br = round_spinor(a, prec), round_spinor(b, prec)
+    tol = 1e-13 if prec == 0 else 1e-6
+    n2 = op.norm2(fa)
+    assert abs(n2 - np.vdot(ar, ar).real) < tol * n2
+    z = op.inner(fa, fb)
+    zr = np.vdot(ar, br)
+    assert abs(z - zr) < tol * np.sqrt(n2 * np.vdot(br, br).real)
+    assert op.norm2(fa) == n2  # bitwise reproducible
+
+
+# ---------------------------------------------------------------- solvers
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+def test_cg_solves_full_system(dwf, oracle_lib, mode):
+    dims, Ls = (4, 4, 4, 4), 8
+    op, U = make(dwf, dims, Ls, 91, eps=0.4)
+    b = synth.random_spinor(dims, Ls, seed=92)
+    fb = op.pack(dev(b), 0, dwf.FULL)
+    x, st = op.cg(fb, tol=1e-10, maxiter=5000, mode=mode)
+    assert st.converged and st.true_residual <= 1e-10
+    xs = host(op.unpack(x))
+    # the oracle recomputes the residual of the full system and the Schur normal equations
+    r = b - oracle_lib.m(dims, Ls, M5, MASS, BC, U, xs)
+    assert np.linalg.norm(r) / np.linalg.norm(b) < 1e-8
+    xo, it, res, ok = oracle_lib.schur_cg(dims, Ls, M5, MASS, BC, U, b, tol=1e-12, maxiter=20000)
+    assert ok
+    assert rel(xs, xo) < 1e-7
+
+
+# ---------------------------------------------------------------- force
+
+
+@pytest.mark.parametrize("dims,Ls", [((4, 4, 4, 4), 4), ((2, 4, 2, 6), 3), ((4, 2, 4, 2), 16)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_force_parity(dwf, oracle_lib, dims, Ls, prec):
+    op, U = make(dwf, dims, Ls, 101)
+    psi = synth.random_spinor(dims, Ls, seed=102)
+    f = op.pack(dev(psi), prec, dwf.FULL)
+    S, F, G = op.force(f)
+    psi_r, U_r = round_spinor(psi, prec), round_spinor(U, prec)
+    S_ref, F_ref, G_ref = oracle_lib.force(dims, Ls, M5, MASS, BC, U_r, psi_r)
+    tol = 1e-12 if prec == 0 else 2e-5
+    assert abs(S - S_ref) < tol * S_ref
+    assert rel(host(F), F_ref) < tol
+    assert rel(host(G), G_ref) < tol
+
+
+def test_autograd_gradients_match_oracle(dwf, oracle_lib):
+    dims, Ls = (4, 2, 2, 4), 4
+    U = synth.random_gauge(dims, seed=111)
+    psi = synth.random_spinor(dims, Ls, seed=112)
+    op = dwf.GridDWF(dims, Ls, M5, MASS, bc=BC)
+    pt = dev(psi).requires_grad_(True)
+    Ut = dev(U).requires_grad_(True)
+    S = dwf.dwf_action(pt, Ut, op)
+    S.backward()
+    S_ref, F_ref, G_ref = oracle_lib.force(dims, Ls, M5, MASS, BC, U, psi)
+    chi = oracle_lib.m(dims, Ls, M5, MASS, BC, U, psi)
+    gpsi_ref = 2.0 * oracle_lib.m(dims, Ls, M5, MASS, BC, U, chi, dag=True)
+    assert abs(S.item() - S_ref) < 1e-12 * S_ref
+    assert rel(host(pt.grad), gpsi_ref) < 1e-12
+    assert rel(host(Ut.grad), G_ref) < 1e-12
+
+
+def test_autograd_gradcheck(dwf):
+    dims, Ls = (2, 2, 2, 2), 2
+    U = dev(synth.random_gauge(dims, seed=121)).requires_grad_(True)
+    psi = dev(synth.random_spinor(dims, Ls, seed=122)).requires_grad_(True)
+    op = dwf.GridDWF(dims, Ls, M5, MASS, bc=BC)
+    assert torch.autograd.gradcheck(lambda p, u: dwf.dwf_action(p, u, op), (psi, U), eps=1e-6, atol=1e-5, rtol=1e-6)
+
+
+# ---------------------------------------------------------------- errors are reported, not raised on the GPU
+
+
+def test_argument_errors(dwf):
+    dims, Ls = (4, 4, 4, 4), 4
+    op, _ = make(dwf, dims, Ls, 131)
+    f = op.field(0, dwf.FULL, zero=True)
+    with pytest.raises(dwf.GridDWFError) as e:
+        op.dhop(f, dwf.FULL, out=f)  # in == out
+    assert e.value.code == -6
+    with pytest.raises(dwf.GridDWFError) as e:
+        op._call("grid_dwf_dhop", 0, dwf._ptr(f.data_ptr() + 8), dwf._ptr(f), 2, 0)  # misaligned
+    assert e.value.code == -1
+    op2 = dwf.GridDWF(dims, Ls, M5, MASS)
+    with pytest.raises(dwf.GridDWFError) as e:
+        op2.dhop(f, dwf.FULL)  # no gauge field yet
+    assert e.value.code == -7
+    b = op.field(0, dwf.FULL, zero=True)
+    b[0] = float("nan")
+    with pytest.raises(dwf.GridDWFError) as e:
+        op.cg(b, tol=1e-10, maxiter=10)
+    assert e.value.code == -5
+    b = op.pack(dev(synth.random_spinor(dims, Ls, seed=132)), 0, dwf.FULL)
+    x, st = op.cg(b, tol=1e-14, maxiter=3, raise_on_fail=False)
+    assert not st.converged and st.iterations == 3
