@@ -58,6 +58,38 @@ def peaks():
 FP64_ALU_TFLOPS = 1.17
 
 
+KERNEL_SOURCES = ["paper_2203_06777_gb300/csrc/dhop_kernel.cuh", "paper_2203_06777_gb300/csrc/dhop_inst.cuh",
+                  "paper_2203_06777_gb300/csrc/dwf_common.cuh", "paper_2203_06777_gb300/csrc/dhop_p32.cu"]
+TRAFFIC_PROFILE = "profiles/dhop_fp32_16x16x16x16_ls16.md"
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic():
+    """DRAM bytes per launch of the FP32 Dhop kernel from the committed ncu summary, if that
+    capture was taken of the kernel sources as they are now; otherwise None."""
+    try:
+        text = open(os.path.join(ROOT, TRAFFIC_PROFILE)).read()
+    except OSError:
+        return None
+    fields = dict(line.split(":", 1) for line in text.splitlines() if line.startswith(("traffic_bytes_per_launch:",
+                                                                                       "source_hash:")))
+    if fields.get("source_hash", "").strip() != kernel_source_hash():
+        return None
+    try:
+        return float(fields["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def algorithmic_bytes_per_site(real_bytes: int, Ls: int) -> float:
     """Each input spinor read once, each output written once, 8 links per 4D site amortised over Ls."""
     return real_bytes * (24 + 24) + 8 * 18 * real_bytes / Ls
@@ -81,7 +113,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -133,15 +165,22 @@ def dist_env():
     return world, rank, local
 
 
-def reduce_max(value: float, world: int, device=None) -> float:
+def reduce_max(value: float, world: int) -> float:
+    """Max over ranks (the job's time is its slowest rank's); a no-op at world size 1."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
 
+    device = "cuda" if dist.get_backend() == "nccl" else "cpu"
     t = torch.tensor([value], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Whole-job rate: the units every rank processed, divided by the slowest rank's time."""
+    return units_per_rank * world / seconds_max
 
 
 def barrier(world: int):
@@ -303,9 +342,13 @@ def gpu_arm(args):
     variants = {}
     results = {}
     clocks = None
+    e2e = None
+    wanted = args.variants.split(",")
     for name, prec, rb in (("f32", dwf.FP32, 4), ("f64", dwf.FP64, 8), ("f16", dwf.FP16, 2), ("bf16", dwf.BF16, 2)):
+        if name not in wanted:
+            continue
         sets = make_sets(dwf, torch, spec, prec, 3, seed0=0)
-        steps = args.steps if name == "f32" else max(3, args.steps // (4 if name == "f64" else 1))
+        steps = args.steps if name != "f64" else max(3, args.steps // 40)
         if name == "f32":
             with ClockSampler(torch.cuda.current_device()) as cs:
                 secs, launches = time_dhop(dwf, torch, sets, steps, args.warmup, world)
@@ -323,20 +366,25 @@ def gpu_arm(args):
         if name == "f64":
             rec["alu_frac"] = round(gflops / (FP64_ALU_TFLOPS * 1e3), 4)
             rec["bound"] = "alu"
+            rec["alu_peak_gflops"] = FP64_ALU_TFLOPS * 1e3
         results[name] = (secs, steps, launches, per_launch, gbs, gflops)
         variants[name] = rec
         if name == "f32":
-            e2e_secs, hb, db = time_dhop_e2e(dwf, torch, sets, max(3, args.steps // 4), args.warmup, world)
+            e2e_steps = max(3, args.steps // 20)
+            e2e_secs, hb, db = time_dhop_e2e(dwf, torch, sets, e2e_steps, args.warmup, world)
             e2e_secs = reduce_max(e2e_secs, world)
-            e2e_steps = max(3, args.steps // 4)
             e2e = {"value": round(world * FLOPS_PER_SITE * 2 * n5 * e2e_steps / e2e_secs / 1e9, 1), "unit": "GFlop/s",
-                   "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db}
-        for s in sets:
-            s[0].close()
+                   "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db, "steps": e2e_steps}
+        for st in sets:
+            st[0].close()
         del sets
         torch.cuda.empty_cache()
+    if "f32" not in results:
+        if rank == 0:
+            print(json.dumps({"variants": variants}), flush=True)
+        return
     secs, steps, launches, per_launch, gbs, gflops = results["f32"]
-    value = world * FLOPS_PER_SITE * 2 * n5 * steps / secs / 1e9
+    value = job_throughput(FLOPS_PER_SITE * 2 * n5 * steps, world, secs) / 1e9
     line = {
         "metric": METRIC,
         "value": round(value, 1),
@@ -354,8 +402,10 @@ def gpu_arm(args):
                    "bc": list(BC), "step": "DhopEO + DhopOE", "parallelism": f"replicas x{world}",
                    "l2": "3 rotating operator+field sets (663 MB FP32) > L2"},
         "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-                     "frac": round(gbs / hbm_peak, 4), "traffic": None, "peak_kind": peak_kind,
-                     "kernel": "dhop_kernel<FP32, ST=2>", "bytes_per_launch": algorithmic_bytes_per_site(4, Ls) * n5},
+                     "frac": round(gbs / hbm_peak, 4), "traffic": measured_traffic(), "peak_kind": peak_kind,
+                     "kernel": "dhop_kernel<FP32> (DhopEO / DhopOE)",
+                     "bytes_per_launch": algorithmic_bytes_per_site(4, Ls) * n5,
+                     "source_hash": kernel_source_hash()},
         "variants": variants,
         "e2e": e2e,
         "gpu_launches": launches,
@@ -414,8 +464,9 @@ def reference_arm(args):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--variants", default="f32,f64,f16,bf16", help="comma list of f32,f64,f16,bf16")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cg", action="store_true", help="skip the CG time-to-solution comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")

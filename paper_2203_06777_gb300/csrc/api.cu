@@ -139,10 +139,7 @@ int ensure_gauge(grid_dwf_t* h, int prec) {
   return GRID_DWF_OK;
 }
 
-int choose_st(int prec, int Ls) {
-  if (prec == GRID_DWF_FP64) return 1;
-  return (Ls % 2 == 0) ? 2 : 1;
-}
+int choose_st(int prec, int Ls) { return dhop_slices_per_thread(prec, dhop_ls_specialised(Ls) ? Ls : 0); }
 
 // One half-lattice hopping application with its fused epilogue.
 int dhop_half(grid_dwf_t* h, int prec, const void* in, void* out, int out_parity, bool dag, int pre, int post,
@@ -158,7 +155,7 @@ int dhop_half(grid_dwf_t* h, int prec, const void* in, void* out, int out_parity
   a.out_parity = out_parity;
   const int st = choose_st(prec, h->Ls);
   a.nsg = h->Ls / st;
-  a.sites_per_cta = 256 / a.nsg;
+  a.sites_per_cta = 128 / a.nsg;
   if (a.sites_per_cta < 1) a.sites_per_cta = 1;
   a.pre = pre;
   a.post = post;

@@ -4,9 +4,9 @@
 
 namespace gdwf {
 
-template <int ST, bool DAG, bool C12>
+template <int ST, bool DAG, bool C12, int LSC>
 static cudaError_t launch_one(const DhopArgs& a, int threads, int blocks, size_t smem, cudaStream_t stream) {
-  auto kern = dhop_kernel<DWF_PREC, ST, DAG, C12>;
+  auto kern = dhop_kernel<DWF_PREC, ST, DAG, C12, LSC>;
   if (smem > 48 * 1024) {
     static size_t configured = 0;  // per instantiation
     if (smem > configured) {
@@ -19,19 +19,29 @@ static cudaError_t launch_one(const DhopArgs& a, int threads, int blocks, size_t
   return cudaGetLastError();
 }
 
+template <int LSC>
+static cudaError_t launch_ls(const DhopArgs& a, bool dag, bool c12, int threads, int blocks, size_t smem,
+                             cudaStream_t stream) {
+  constexpr int ST = dhop_slices_per_thread(DWF_PREC, LSC);
+  if (dag) return c12 ? launch_one<ST, true, true, LSC>(a, threads, blocks, smem, stream)
+                      : launch_one<ST, true, false, LSC>(a, threads, blocks, smem, stream);
+  return c12 ? launch_one<ST, false, true, LSC>(a, threads, blocks, smem, stream)
+             : launch_one<ST, false, false, LSC>(a, threads, blocks, smem, stream);
+}
+
 template <>
 cudaError_t launch_dhop<DWF_PREC>(const DhopArgs& a, int st, bool dag, bool c12, int threads, int blocks, size_t smem,
                                   cudaStream_t stream) {
-#define DWF_DISPATCH(ST_)                                                         \
-  if (dag) return c12 ? launch_one<ST_, true, true>(a, threads, blocks, smem, stream) \
-                      : launch_one<ST_, true, false>(a, threads, blocks, smem, stream); \
-  return c12 ? launch_one<ST_, false, true>(a, threads, blocks, smem, stream)         \
-             : launch_one<ST_, false, false>(a, threads, blocks, smem, stream);
-  if (st == 2) {
-    DWF_DISPATCH(2)
+  if (st != dhop_slices_per_thread(DWF_PREC, dhop_ls_specialised(a.g.Ls) ? a.g.Ls : 0)) return cudaErrorInvalidValue;
+  switch (a.g.Ls) {
+#define DWF_CASE(L_) \
+  case L_:           \
+    return launch_ls<L_>(a, dag, c12, threads, blocks, smem, stream);
+    DWF_LS_SPECIALISATIONS(DWF_CASE)
+#undef DWF_CASE
+    default:
+      return launch_ls<0>(a, dag, c12, threads, blocks, smem, stream);
   }
-  DWF_DISPATCH(1)
-#undef DWF_DISPATCH
 }
 
 }  // namespace gdwf

@@ -92,59 +92,82 @@ __device__ __forceinline__ void project(int mu, const R* psi, R* h) {
 #undef PI
 }
 
-// acc += reconstruct(uh): upper spins take uh, lower spins the matching multiple of it.
+template <typename R>
+__device__ __forceinline__ R fma_r(R a, R b, R c);
+template <>
+__device__ __forceinline__ float fma_r<float>(float a, float b, float c) {
+  return fmaf(a, b, c);
+}
+template <>
+__device__ __forceinline__ double fma_r<double>(double a, double b, double c) {
+  return fma(a, b, c);
+}
+
+// acc += c * reconstruct(uh): upper spins take uh, lower spins the matching multiple of it.
+// c carries the boundary phase and any overall scale, so each term is one FMA.
 template <int SIG, typename R>
-__device__ __forceinline__ void accumulate(int mu, const R* uh, R* acc) {
+__device__ __forceinline__ void accumulate(int mu, const R* uh, R c, R* acc) {
+  const R cs = SIG * c;
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const R a0r = uh[(0 * 3 + c) * 2], a0i = uh[(0 * 3 + c) * 2 + 1];
-    const R a1r = uh[(1 * 3 + c) * 2], a1i = uh[(1 * 3 + c) * 2 + 1];
-    acc[(0 * 3 + c) * 2] += a0r;
-    acc[(0 * 3 + c) * 2 + 1] += a0i;
-    acc[(1 * 3 + c) * 2] += a1r;
-    acc[(1 * 3 + c) * 2 + 1] += a1i;
-    R* s2 = acc + (2 * 3 + c) * 2;
-    R* s3 = acc + (3 * 3 + c) * 2;
+  for (int k = 0; k < 3; ++k) {
+    const R a0r = uh[(0 * 3 + k) * 2], a0i = uh[(0 * 3 + k) * 2 + 1];
+    const R a1r = uh[(1 * 3 + k) * 2], a1i = uh[(1 * 3 + k) * 2 + 1];
+    R* s0 = acc + (0 * 3 + k) * 2;
+    R* s1 = acc + (1 * 3 + k) * 2;
+    R* s2 = acc + (2 * 3 + k) * 2;
+    R* s3 = acc + (3 * 3 + k) * 2;
+    s0[0] = fma_r(c, a0r, s0[0]);
+    s0[1] = fma_r(c, a0i, s0[1]);
+    s1[0] = fma_r(c, a1r, s1[0]);
+    s1[1] = fma_r(c, a1i, s1[1]);
     if (mu == 0) {  // spin2 += SIG i uh1, spin3 += SIG i uh0
-      s2[0] -= SIG * a1i;
-      s2[1] += SIG * a1r;
-      s3[0] -= SIG * a0i;
-      s3[1] += SIG * a0r;
+      s2[0] = fma_r(-cs, a1i, s2[0]);
+      s2[1] = fma_r(cs, a1r, s2[1]);
+      s3[0] = fma_r(-cs, a0i, s3[0]);
+      s3[1] = fma_r(cs, a0r, s3[1]);
     } else if (mu == 1) {  // spin2 += SIG uh1, spin3 -= SIG uh0
-      s2[0] += SIG * a1r;
-      s2[1] += SIG * a1i;
-      s3[0] -= SIG * a0r;
-      s3[1] -= SIG * a0i;
+      s2[0] = fma_r(cs, a1r, s2[0]);
+      s2[1] = fma_r(cs, a1i, s2[1]);
+      s3[0] = fma_r(-cs, a0r, s3[0]);
+      s3[1] = fma_r(-cs, a0i, s3[1]);
     } else if (mu == 2) {  // spin2 += SIG i uh0, spin3 -= SIG i uh1
-      s2[0] -= SIG * a0i;
-      s2[1] += SIG * a0r;
-      s3[0] += SIG * a1i;
-      s3[1] -= SIG * a1r;
+      s2[0] = fma_r(-cs, a0i, s2[0]);
+      s2[1] = fma_r(cs, a0r, s2[1]);
+      s3[0] = fma_r(cs, a1i, s3[0]);
+      s3[1] = fma_r(-cs, a1r, s3[1]);
     } else {  // spin2 += SIG uh0, spin3 += SIG uh1
-      s2[0] += SIG * a0r;
-      s2[1] += SIG * a0i;
-      s3[0] += SIG * a1r;
-      s3[1] += SIG * a1i;
+      s2[0] = fma_r(cs, a0r, s2[0]);
+      s2[1] = fma_r(cs, a0i, s2[1]);
+      s3[0] = fma_r(cs, a1r, s3[0]);
+      s3[1] = fma_r(cs, a1i, s3[1]);
     }
   }
 }
 
-// o = U h (DAGGER = false) or U^+ h, for both spins of the half spinor. u: row-major 3x3 complex.
+// o = U h (DAGGER = false) or U^+ h, for both spins of the half spinor; u row-major 3x3 complex.
+// Written as explicit FMA chains: 12 instructions per complex output.
 template <bool DAGGER, typename R>
 __device__ __forceinline__ void su3_mul(const R* u, const R* h, R* o) {
 #pragma unroll
   for (int sp = 0; sp < 2; ++sp)
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      R re = 0, im = 0;
+      R re, im;
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
         const int e = DAGGER ? (b * 3 + a) : (a * 3 + b);
         const R ur = u[e * 2];
         const R ui = DAGGER ? -u[e * 2 + 1] : u[e * 2 + 1];
         const R hr = h[(sp * 3 + b) * 2], hi = h[(sp * 3 + b) * 2 + 1];
-        re += ur * hr - ui * hi;
-        im += ur * hi + ui * hr;
+        if (b == 0) {
+          re = ur * hr;
+          im = ur * hi;
+        } else {
+          re = fma_r(ur, hr, re);
+          im = fma_r(ur, hi, im);
+        }
+        re = fma_r(-ui, hi, re);
+        im = fma_r(ui, hr, im);
       }
       o[(sp * 3 + a) * 2] = re;
       o[(sp * 3 + a) * 2 + 1] = im;
@@ -181,20 +204,25 @@ __device__ __forceinline__ void load_link(const char* p, typename Store<P>::R* u
   }
 }
 
-template <int P>
-__device__ __forceinline__ void load_spinor(const char* site_block, int s, int Ls, typename Store<P>::R* psi) {
+// Slice s of a site block. LSC > 0 fixes Ls at compile time (immediate chunk offsets).
+template <int P, int LSC = 0>
+__device__ __forceinline__ void load_spinor(const char* site_block, int s, int Ls_rt, typename Store<P>::R* psi) {
   constexpr int VEC = Store<P>::VEC;
   constexpr int NCH = 24 / VEC;
+  const int Ls = LSC > 0 ? LSC : Ls_rt;
+  const char* b = site_block + (size_t)s * 16;
 #pragma unroll
-  for (int k = 0; k < NCH; ++k) ld16<P>(site_block + ((size_t)k * Ls + s) * 16, psi + k * VEC);
+  for (int k = 0; k < NCH; ++k) ld16<P>(b + (size_t)k * Ls * 16, psi + k * VEC);
 }
 
-template <int P>
-__device__ __forceinline__ void store_spinor(char* site_block, int s, int Ls, const typename Store<P>::R* v) {
+template <int P, int LSC = 0>
+__device__ __forceinline__ void store_spinor(char* site_block, int s, int Ls_rt, const typename Store<P>::R* v) {
   constexpr int VEC = Store<P>::VEC;
   constexpr int NCH = 24 / VEC;
+  const int Ls = LSC > 0 ? LSC : Ls_rt;
+  char* b = site_block + (size_t)s * 16;
 #pragma unroll
-  for (int k = 0; k < NCH; ++k) st16<P>(site_block + ((size_t)k * Ls + s) * 16, v + k * VEC);
+  for (int k = 0; k < NCH; ++k) st16<P>(b + (size_t)k * Ls * 16, v + k * VEC);
 }
 
 // (Mooee aux)_s or (Mooee^+ aux)_s for one slice: the upper (P+) reals couple to s-1 and the
@@ -256,21 +284,22 @@ __device__ __forceinline__ void mooee_inv_line(R* v, int Ls, bool forward_form, 
   }
 }
 
-template <int P, int ST, bool DAG, bool C12>
-__global__ void __launch_bounds__(256) dhop_kernel(const __grid_constant__ DhopArgs a) {
+template <int P, int ST, bool DAG, bool C12, int LSC>
+__device__ __forceinline__ void dhop_body(const DhopArgs& a) {
   using T = typename Store<P>::T;
   using R = typename Store<P>::R;
   constexpr int LB = link_bytes(sizeof(T), C12);
   constexpr int SF = DAG ? +1 : -1;  // forward projector (1 + SF gamma)
   constexpr int SB = -SF;            // backward projector
-  const int Ls = a.g.Ls;
-  const int nsg = a.nsg;
+  const int Ls = LSC > 0 ? LSC : a.g.Ls;
+  const int nsg = LSC > 0 ? LSC / ST : a.nsg;
   const int tid = threadIdx.x;
   const int site_local = tid / nsg;
   const int sg = tid - site_local * nsg;
   const int site = blockIdx.x * a.sites_per_cta + site_local;
   const bool active = site_local < a.sites_per_cta && site < a.g.N4h;
   const size_t site_bytes = (size_t)Ls * 24 * sizeof(T);
+  const R alpha = R(a.alpha);
 
   R acc[ST][24];
 #pragma unroll
@@ -292,17 +321,14 @@ __global__ void __launch_bounds__(256) dhop_kernel(const __grid_constant__ DhopA
         R u[18];
         load_link<P, C12>(Uo + ((size_t)site * 4 + mu) * LB, u);
         const char* pj = in + (size_t)j * site_bytes;
+        const R scale = ph < 0 ? -alpha : alpha;
 #pragma unroll
         for (int k = 0; k < ST; ++k) {
           R psi[24], h[12], uh[12];
-          load_spinor<P>(pj, sg + k * nsg, Ls, psi);
+          load_spinor<P, LSC>(pj, sg + k * nsg, Ls, psi);
           project<SF>(mu, psi, h);
-          if (ph < 0) {
-#pragma unroll
-            for (int r = 0; r < 12; ++r) h[r] = -h[r];
-          }
           su3_mul<false>(u, h, uh);
-          accumulate<SF>(mu, uh, acc[k]);
+          accumulate<SF>(mu, uh, scale, acc[k]);
         }
       }
       {  // backward hop: (1 + SB gamma_mu) U_mu(x - mu)^+ psi(x - mu)
@@ -311,49 +337,42 @@ __global__ void __launch_bounds__(256) dhop_kernel(const __grid_constant__ DhopA
         R u[18];
         load_link<P, C12>(Ui + ((size_t)j * 4 + mu) * LB, u);
         const char* pj = in + (size_t)j * site_bytes;
+        const R scale = ph < 0 ? -alpha : alpha;
 #pragma unroll
         for (int k = 0; k < ST; ++k) {
           R psi[24], h[12], uh[12];
-          load_spinor<P>(pj, sg + k * nsg, Ls, psi);
+          load_spinor<P, LSC>(pj, sg + k * nsg, Ls, psi);
           project<SB>(mu, psi, h);
-          if (ph < 0) {
-#pragma unroll
-            for (int r = 0; r < 12; ++r) h[r] = -h[r];
-          }
           su3_mul<true>(u, h, uh);
-          accumulate<SB>(mu, uh, acc[k]);
+          accumulate<SB>(mu, uh, scale, acc[k]);
         }
       }
     }
   }
 
   // ------------------------------------------------------------ epilogue
-  const R alpha = R(a.alpha), beta = R(a.beta);
+  const R beta = R(a.beta);
   const char* auxb = a.pre != PRE_NONE ? static_cast<const char*>(a.aux) + (size_t)site * site_bytes : nullptr;
   char* outb = static_cast<char*>(a.out) + (size_t)site * site_bytes;
-  if (active) {
+  if (active && a.pre != PRE_NONE) {
 #pragma unroll
     for (int k = 0; k < ST; ++k) {
       const int s = sg + k * nsg;
+      R o[24];
+      if (a.pre == PRE_AUX)
+        load_spinor<P, LSC>(auxb, s, Ls, o);
+      else if (a.pre == PRE_MOOEE)
+        mooee_slice<P, false>(auxb, s, Ls, a.d5, a.mass, o);
+      else
+        mooee_slice<P, true>(auxb, s, Ls, a.d5, a.mass, o);
 #pragma unroll
-      for (int r = 0; r < 24; ++r) acc[k][r] *= alpha;
-      if (a.pre != PRE_NONE) {
-        R o[24];
-        if (a.pre == PRE_AUX)
-          load_spinor<P>(auxb, s, Ls, o);
-        else if (a.pre == PRE_MOOEE)
-          mooee_slice<P, false>(auxb, s, Ls, a.d5, a.mass, o);
-        else
-          mooee_slice<P, true>(auxb, s, Ls, a.d5, a.mass, o);
-#pragma unroll
-        for (int r = 0; r < 24; ++r) acc[k][r] += beta * o[r];
-      }
+      for (int r = 0; r < 24; ++r) acc[k][r] = fma_r(beta, o[r], acc[k][r]);
     }
   }
   if (a.post == POST_NONE) {
     if (active) {
 #pragma unroll
-      for (int k = 0; k < ST; ++k) store_spinor<P>(outb, sg + k * nsg, Ls, acc[k]);
+      for (int k = 0; k < ST; ++k) store_spinor<P, LSC>(outb, sg + k * nsg, Ls, acc[k]);
     }
     return;
   }
@@ -383,12 +402,35 @@ __global__ void __launch_bounds__(256) dhop_kernel(const __grid_constant__ DhopA
 #pragma unroll
     for (int k = 0; k < ST; ++k) {
       const int s = sg + k * nsg;
-      store_spinor<P>(outb, s, Ls, sm + ((size_t)site_local * Ls + s) * 24);
+      store_spinor<P, LSC>(outb, s, Ls, sm + ((size_t)site_local * Ls + s) * 24);
     }
   }
 }
 
-// Host-side launcher, instantiated once per storage precision in its own translation unit.
+// Register budget: at most 256 threads per CTA and two such CTAs per SM (128 registers per
+// thread): the measured optimum for the FP32 and 16-bit kernels on GB300 (more resident warps
+// with fewer registers spill and run slower). The FP64 kernel is bound by the FP64 pipe and
+// keeps more registers instead.
+template <int P>
+struct DhopOccupancy {
+  static constexpr int MIN_BLOCKS = (P == P64) ? 1 : 2;
+};
+
+// Slices per thread: two for the 16-bit storage formats at a compile-time Ls (halves the link
+// loads and conversions per slice), one otherwise.
+__host__ __device__ constexpr int dhop_slices_per_thread(int prec, int lsc) {
+  return (lsc > 0 && (prec == P16 || prec == PB16)) ? 2 : 1;
+}
+
+// Ls values with a compile-time specialisation; any other Ls runs the generic kernel (LSC = 0).
+#define DWF_LS_SPECIALISATIONS(M) M(8) M(12) M(16) M(24) M(32)
+inline bool dhop_ls_specialised(int Ls) { return Ls == 8 || Ls == 12 || Ls == 16 || Ls == 24 || Ls == 32; }
+
+template <int P, int ST, bool DAG, bool C12, int LSC>
+__global__ void __launch_bounds__(256, DhopOccupancy<P>::MIN_BLOCKS) dhop_kernel(const __grid_constant__ DhopArgs a) {
+  dhop_body<P, ST, DAG, C12, LSC>(a);
+}
+
 template <int P>
 cudaError_t launch_dhop(const DhopArgs& a, int st, bool dag, bool c12, int threads, int blocks, size_t smem,
                         cudaStream_t stream);
