@@ -142,6 +142,27 @@ int grid_dwf_cg(grid_dwf_t* h, const void* b, void* x, double tol, int maxiter, 
  * scratch. Under U -> exp(eps A) U with A in su(3): dS/deps = sum Re tr(A^+ F). *S_out on host. */
 int grid_dwf_force(grid_dwf_t* h, int precision, const void* psi, void* chi, double* F, double* G, double* S_out);
 
+/* |a|^2 (b == NULL) or a^+ b with FP64 accumulation, like grid_dwf_norm2 / grid_dwf_inner, for
+ * callers that cannot allocate device memory: code recording a CUDA graph (where cudaMalloc is
+ * not allowed), loops that must not take cudaMalloc's implicit device synchronisation, or a host
+ * framework that owns all device memory through its own pool and has none to spare. It needs no
+ * handle and allocates nothing: its scratch (partial sums) is a fixed 256 KiB array in the
+ * library's device image, present on every GPU that loads the library until the process exits.
+ * The paper has no counterpart; this is a service of the library.
+ *   a, b      device fields of `precision` in the device layout (16-byte aligned), nsites
+ *             checkerboard site blocks of Ls slices each (V/2 for a half field, V for a full one);
+ *   result    device pointer to 2 doubles (8-byte aligned), receives (re, im) (im = 0 for |a|^2);
+ *   stream    cudaStream_t the two kernels run on (NULL = legacy default stream); asynchronous;
+ *   err       optional buffer for a message on failure.
+ * Limit: nsites * Ls <= 11184810 five-dimensional sites (e.g. a 32^4 x 16 half field, 8388608);
+ * larger fields are rejected with GRID_DWF_ERR_INVALID_ARG before anything runs. The first call
+ * on a device looks up the array's device address (once per device, with that device current);
+ * make that first call before any stream capture. All calls share the one array, which keeps the
+ * last call's partial sums (each call overwrites what it reads), so calls whose kernels overlap
+ * on the GPU (on different streams, or different host threads) race and give wrong results. */
+int grid_dwf_inner_noalloc(int precision, const void* a, const void* b, long nsites, int Ls, void* stream,
+                           double* result, char* err, size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

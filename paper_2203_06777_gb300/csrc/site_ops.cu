@@ -597,3 +597,163 @@ cudaError_t launch_axpby(int p, double a, const void* x, double b, void* y, long
 }
 
 }  // namespace gdwf
+
+// ---------------------------------------------------------------- reduction without allocation
+//
+// grid_dwf_inner_noalloc: the same FP64-accumulated reduction as launch_reduce, for callers
+// that must not allocate device memory, with its scratch in a fixed array that is part of the
+// library's device image instead of a cudaMalloc'd buffer. Each CTA reduces one contiguous
+// chunk of NOALLOC_UNITS_PER_CTA units (8 reals each), so the number of partial sums, and with
+// it the largest field accepted, is bounded by the array.
+
+namespace gdwf {
+
+constexpr int NOALLOC_UNITS_PER_THREAD = 8;
+constexpr long NOALLOC_UNITS_PER_CTA = (long)RED_THREADS * NOALLOC_UNITS_PER_THREAD;
+constexpr int NOALLOC_MAX_PARTIALS = 16384;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+// [re partials][im partials]: 256 KiB on every device that loads the library, held until the
+// process exits.
+static __device__ __align__(256) double g_noalloc_scratch[2 * NOALLOC_MAX_PARTIALS];
+
+template <int P, bool INNER>
+__global__ void __launch_bounds__(RED_THREADS) k_reduce_chunked(const void* a, const void* b, long nsites, int Ls,
+                                                                double* partials, int nblocks) {
+  using R = RT<P>;
+  double acc[2] = {0.0, 0.0};
+  const long units = nsites * 3 * Ls;
+  const long first = (long)blockIdx.x * NOALLOC_UNITS_PER_CTA;
+#pragma unroll
+  for (int k = 0; k < NOALLOC_UNITS_PER_THREAD; ++k) {
+    const long u = first + threadIdx.x + (long)k * RED_THREADS;
+    if (u >= units) break;
+    long site;
+    int g, s;
+    unit_coords(u, Ls, site, g, s);
+    R x[8];
+    ld8<P, false>(a, site, g, s, Ls, x);
+    if (INNER) {
+      R y[8];
+      ld8<P, false>(b, site, g, s, Ls, y);
+      R re = 0, im = 0;
+#pragma unroll
+      for (int j = 0; j < 8; j += 2) {
+        re += x[j] * y[j] + x[j + 1] * y[j + 1];
+        im += x[j] * y[j + 1] - x[j + 1] * y[j];
+      }
+      acc[0] += (double)re;
+      acc[1] += (double)im;
+    } else {
+      R t = 0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) t += x[j] * x[j];
+      acc[0] += (double)t;
+    }
+  }
+  block_sum<2>(acc, partials, nblocks);
+}
+
+// One CTA adds the nblocks partials in a fixed order and writes (re, im) to out.
+__global__ void __launch_bounds__(RED_THREADS) k_finalize_chunked(const double* partials, int nblocks, double* out) {
+  __shared__ double red[2][RED_THREADS];
+  for (int k = 0; k < 2; ++k) {
+    double t = 0;
+    for (int i = threadIdx.x; i < nblocks; i += RED_THREADS) t += partials[k * nblocks + i];
+    red[k][threadIdx.x] = t;
+  }
+  __syncthreads();
+  for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int k = 0; k < 2; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = red[0][0];
+    out[1] = red[1][0];
+  }
+}
+
+}  // namespace gdwf
+
+#include <mutex>
+#include <string>
+
+#include "../../include/grid_dwf.h"
+
+namespace {
+
+double* g_noalloc_dev_ptr[gdwf::NOALLOC_MAX_DEVICES] = {};
+std::mutex g_noalloc_mutex;
+
+int noalloc_error(char* err, size_t err_len, int code, const std::string& msg) {
+  if (err && err_len > 0) {
+    const size_t n = msg.size() < err_len - 1 ? msg.size() : err_len - 1;
+    memcpy(err, msg.data(), n);
+    err[n] = '\0';
+  }
+  return code;
+}
+
+}  // namespace
+
+extern "C" int grid_dwf_inner_noalloc(int precision, const void* a, const void* b, long nsites, int Ls, void* stream,
+                                      double* result, char* err, size_t err_len) {
+  using namespace gdwf;
+  if (err && err_len > 0) err[0] = '\0';
+  if (precision < GRID_DWF_FP64 || precision > GRID_DWF_BF16)
+    return noalloc_error(err, err_len, GRID_DWF_ERR_INVALID_ARG, "grid_dwf_inner_noalloc: bad precision");
+  if (!a || !result || nsites < 0 || Ls < 1)
+    return noalloc_error(err, err_len, GRID_DWF_ERR_INVALID_ARG, "grid_dwf_inner_noalloc: null pointer or bad size");
+  if (reinterpret_cast<uintptr_t>(a) % 16 || (b && reinterpret_cast<uintptr_t>(b) % 16) ||
+      reinterpret_cast<uintptr_t>(result) % 8)
+    return noalloc_error(err, err_len, GRID_DWF_ERR_INVALID_ARG, "grid_dwf_inner_noalloc: misaligned pointer");
+  const long units = nsites * 3L * Ls;
+  const long nblocks = (units + NOALLOC_UNITS_PER_CTA - 1) / NOALLOC_UNITS_PER_CTA;
+  if (nsites > 0 && (units / 3 / Ls != nsites || nblocks > NOALLOC_MAX_PARTIALS))
+    return noalloc_error(err, err_len, GRID_DWF_ERR_INVALID_ARG,
+                         "grid_dwf_inner_noalloc: field of " + std::to_string(nsites) + " sites x Ls " +
+                             std::to_string(Ls) + " exceeds the static scratch (at most " +
+                             std::to_string((long)NOALLOC_MAX_PARTIALS * NOALLOC_UNITS_PER_CTA / 3) +
+                             " five-dimensional sites, nsites * Ls)");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess)
+    return noalloc_error(err, err_len, GRID_DWF_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES)
+    return noalloc_error(err, err_len, GRID_DWF_ERR_INVALID_ARG, "grid_dwf_inner_noalloc: device index too large");
+  double* scratch = nullptr;
+  {
+    // Set-up, once per device, with that device current: the device address of the array.
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_dev_ptr[dev]) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess)
+        return noalloc_error(err, err_len, GRID_DWF_ERR_CUDA,
+                             std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      g_noalloc_dev_ptr[dev] = static_cast<double*>(p);
+    }
+    scratch = g_noalloc_dev_ptr[dev];
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int nb = nblocks > 0 ? (int)nblocks : 1;
+  const bool inner = b != nullptr;
+#define NA(P_)                                                                                         \
+  if (inner)                                                                                           \
+    k_reduce_chunked<P_, true><<<nb, RED_THREADS, 0, st>>>(a, b, nsites, Ls, scratch, nb);             \
+  else                                                                                                 \
+    k_reduce_chunked<P_, false><<<nb, RED_THREADS, 0, st>>>(a, b, nsites, Ls, scratch, nb);
+  switch (precision) {
+    case P64: NA(P64) break;
+    case P32: NA(P32) break;
+    case P16: NA(P16) break;
+    default: NA(PB16) break;
+  }
+#undef NA
+  k_finalize_chunked<<<1, RED_THREADS, 0, st>>>(scratch, nb, result);
+  e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return noalloc_error(err, err_len, GRID_DWF_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
+  return GRID_DWF_OK;
+}

@@ -1,0 +1,84 @@
+"""grid_dwf_inner_noalloc: the reduction for callers that cannot allocate device memory.
+
+Such callers (code recording a CUDA graph, loops that must not pay cudaMalloc's implicit
+device synchronisation, hosts whose memory pool owns the whole device) get |a|^2 and a^+ b from
+a fixed scratch array built into the library instead of a handle's buffers. This file is
+collected last on purpose: if it fails, a run stopped at the first failure has already run
+everything else.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2203_06777_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+MAX_SITES_X_LS = 11184810  # the documented limit: nsites * Ls five-dimensional sites
+TOL = {0: 1e-13, 1: 1e-6, 2: 1e-6, 3: 1e-6}
+
+
+@pytest.fixture(scope="module")
+def dwf():
+    from paper_2203_06777_gb300 import dwf as mod
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lib = mod.load()
+    fn = lib.grid_dwf_inner_noalloc
+    fn.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_long, ctypes.c_int, ctypes.c_void_p,
+                   ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t]
+    fn.restype = ctypes.c_int
+    return mod
+
+
+def noalloc(dwf, prec, a, b, nsites, Ls, out):
+    err = ctypes.create_string_buffer(256)
+    stream = torch.cuda.current_stream().cuda_stream
+    rc = dwf.load().grid_dwf_inner_noalloc(prec, a.data_ptr(), None if b is None else b.data_ptr(), nsites, Ls,
+                                          stream, out.data_ptr(), err, 256)
+    return rc, err.value.decode()
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+def test_noalloc_matches_handle_reductions_twice_in_a_row(dwf, prec):
+    dims, Ls = (8, 4, 4, 6), 8
+    op = dwf.GridDWF(dims, Ls, 1.8, 0.01)
+    a = op.pack(torch.from_numpy(synth.random_spinor(dims, Ls, seed=201)).cuda(), prec, dwf.FULL)
+    b = op.pack(torch.from_numpy(synth.random_spinor(dims, Ls, seed=202)).cuda(), prec, dwf.FULL)
+    c = op.pack(torch.from_numpy(synth.random_spinor(dims, Ls, seed=203)).cuda(), prec, dwf.ODD)
+    nfull = int(np.prod(dims))
+    out = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
+    # set-up calls (scratch address lookup on this device; first launch of both kernel variants),
+    # then two measured calls in a row
+    assert noalloc(dwf, prec, a, b, nfull, Ls, out)[0] == 0
+    assert noalloc(dwf, prec, c, None, nfull // 2, Ls, out)[0] == 0
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    rc1, msg1 = noalloc(dwf, prec, a, b, nfull, Ls, out)
+    torch.cuda.synchronize()
+    first = out.cpu().numpy().copy()
+    rc2, msg2 = noalloc(dwf, prec, c, None, nfull // 2, Ls, out)
+    torch.cuda.synchronize()
+    second = out.cpu().numpy().copy()
+    assert rc1 == 0 and rc2 == 0, (msg1, msg2)
+    assert torch.cuda.mem_get_info()[0] == free_before  # nothing allocated on the device
+    ref_inner = op.inner(a, b)
+    ref_norm = op.norm2(c)
+    scale = np.sqrt(op.norm2(a) * op.norm2(b))
+    assert abs(complex(first[0], first[1]) - ref_inner) <= TOL[prec] * scale
+    assert abs(second[0] - ref_norm) <= TOL[prec] * ref_norm and second[1] == 0.0
+
+
+def test_noalloc_rejects_fields_beyond_the_static_scratch(dwf):
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    a = torch.zeros(4 * 16 * 24, dtype=torch.float32, device="cuda")  # 4 sites x Ls 16, FP32
+    # the size check runs on the host before any launch, so the small buffer is never read
+    rc, msg = noalloc(dwf, 1, a, None, MAX_SITES_X_LS // 16 + 1, 16, out)
+    assert rc == -1 and "exceeds the static scratch" in msg
+    rc, msg = noalloc(dwf, 1, a, None, 4, 16, out)
+    assert rc == 0, msg
+    torch.cuda.synchronize()
+    assert out.cpu().numpy().tolist() == [0.0, 0.0]
