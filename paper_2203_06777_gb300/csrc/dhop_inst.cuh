@@ -1,6 +1,6 @@
 // Instantiates launch_dhop<DWF_PREC>: one translation unit per storage precision so that the
 // kernel variants of the four precisions compile in parallel.
-#include "dhop_kernel.cuh"
+#include "dhop_tma.cuh"
 
 namespace gdwf {
 
@@ -19,10 +19,31 @@ static cudaError_t launch_one(const DhopArgs& a, int threads, int blocks, size_t
   return cudaGetLastError();
 }
 
+template <bool DAG, bool C12, int LSC>
+static cudaError_t launch_tma(const DhopArgs& a, int threads, int blocks, size_t smem, cudaStream_t stream) {
+  auto kern = dhop_tma_kernel<DWF_PREC, DAG, C12, LSC>;
+  static size_t configured = 0;  // per instantiation
+  if (smem > 48 * 1024 && smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  kern<<<blocks, threads, smem, stream>>>(a);
+  return cudaGetLastError();
+}
+
 template <int LSC>
 static cudaError_t launch_ls(const DhopArgs& a, bool dag, bool c12, int threads, int blocks, size_t smem,
                              cudaStream_t stream) {
   constexpr int ST = dhop_slices_per_thread(DWF_PREC, LSC);
+  if constexpr (LSC > 0 && DWF_PREC != P64) {
+    if (a.seg > 0) {
+      if (dag) return c12 ? launch_tma<true, true, LSC>(a, threads, blocks, smem, stream)
+                          : launch_tma<true, false, LSC>(a, threads, blocks, smem, stream);
+      return c12 ? launch_tma<false, true, LSC>(a, threads, blocks, smem, stream)
+                 : launch_tma<false, false, LSC>(a, threads, blocks, smem, stream);
+    }
+  }
   if (dag) return c12 ? launch_one<ST, true, true, LSC>(a, threads, blocks, smem, stream)
                       : launch_one<ST, true, false, LSC>(a, threads, blocks, smem, stream);
   return c12 ? launch_one<ST, false, true, LSC>(a, threads, blocks, smem, stream)
@@ -32,7 +53,8 @@ static cudaError_t launch_ls(const DhopArgs& a, bool dag, bool c12, int threads,
 template <>
 cudaError_t launch_dhop<DWF_PREC>(const DhopArgs& a, int st, bool dag, bool c12, int threads, int blocks, size_t smem,
                                   cudaStream_t stream) {
-  if (st != dhop_slices_per_thread(DWF_PREC, dhop_ls_specialised(a.g.Ls) ? a.g.Ls : 0)) return cudaErrorInvalidValue;
+  if (a.seg == 0 && st != dhop_slices_per_thread(DWF_PREC, dhop_ls_specialised(a.g.Ls) ? a.g.Ls : 0))
+    return cudaErrorInvalidValue;
   switch (a.g.Ls) {
 #define DWF_CASE(L_) \
   case L_:           \

@@ -49,6 +49,8 @@ struct DhopArgs {
   double mass;     // m
   double inv_d5;   // 1 / (5 - M5)
   double inv_den;  // 1 / ((5 - M5) + m (5 - M5)^-(Ls-1))
+  int seg;         // > 0: bulk-copy staged kernel with this many sites per CTA (dhop_tma.cuh)
+  int* status;     // device status word: bit 0 set if a staged kernel's wait timed out
 };
 
 // ---------------------------------------------------------------- spin algebra
@@ -174,6 +176,24 @@ __device__ __forceinline__ void su3_mul(const R* u, const R* h, R* o) {
     }
 }
 
+// Third row of an SU(3) matrix from its first two: row2 = conj(row0 x row1).
+template <typename R>
+__device__ __forceinline__ void reconstruct_row2(R* u) {
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    const int b1 = (b + 1) % 3, b2 = (b + 2) % 3;
+    // row2[b] = conj(row0[b1] row1[b2] - row0[b2] row1[b1])
+    const R xr = u[(0 * 3 + b1) * 2], xi = u[(0 * 3 + b1) * 2 + 1];
+    const R yr = u[(1 * 3 + b2) * 2], yi = u[(1 * 3 + b2) * 2 + 1];
+    const R zr = u[(0 * 3 + b2) * 2], zi = u[(0 * 3 + b2) * 2 + 1];
+    const R wr = u[(1 * 3 + b1) * 2], wi = u[(1 * 3 + b1) * 2 + 1];
+    const R cr = (xr * yr - xi * yi) - (zr * wr - zi * wi);
+    const R ci = (xr * yi + xi * yr) - (zr * wi + zi * wr);
+    u[(2 * 3 + b) * 2] = cr;
+    u[(2 * 3 + b) * 2 + 1] = -ci;
+  }
+}
+
 // Load one link (18 reals; the third row rebuilt as the conjugated cross product of the first
 // two when only 12 are stored, which holds for every SU(3) matrix).
 template <int P, bool C12>
@@ -187,24 +207,9 @@ __device__ __forceinline__ void load_link(const char* p, typename Store<P>::R* u
   for (int v = 0; v < NV; ++v) ld16<P>(p + v * 16, buf + v * VEC);
 #pragma unroll
   for (int i = 0; i < NR; ++i) u[i] = buf[i];
-  if (C12) {
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const int b1 = (b + 1) % 3, b2 = (b + 2) % 3;
-      // row2[b] = conj(row0[b1] row1[b2] - row0[b2] row1[b1])
-      const R xr = u[(0 * 3 + b1) * 2], xi = u[(0 * 3 + b1) * 2 + 1];
-      const R yr = u[(1 * 3 + b2) * 2], yi = u[(1 * 3 + b2) * 2 + 1];
-      const R zr = u[(0 * 3 + b2) * 2], zi = u[(0 * 3 + b2) * 2 + 1];
-      const R wr = u[(1 * 3 + b1) * 2], wi = u[(1 * 3 + b1) * 2 + 1];
-      const R cr = (xr * yr - xi * yi) - (zr * wr - zi * wi);
-      const R ci = (xr * yi + xi * yr) - (zr * wi + zi * wr);
-      u[(2 * 3 + b) * 2] = cr;
-      u[(2 * 3 + b) * 2 + 1] = -ci;
-    }
-  }
+  if (C12) reconstruct_row2(u);
 }
 
-// Slice s of a site block. LSC > 0 fixes Ls at compile time (immediate chunk offsets).
 template <int P, int LSC = 0>
 __device__ __forceinline__ void load_spinor(const char* site_block, int s, int Ls_rt, typename Store<P>::R* psi) {
   constexpr int VEC = Store<P>::VEC;
@@ -223,6 +228,30 @@ __device__ __forceinline__ void store_spinor(char* site_block, int s, int Ls_rt,
   char* b = site_block + (size_t)s * 16;
 #pragma unroll
   for (int k = 0; k < NCH; ++k) st16<P>(b + (size_t)k * Ls * 16, v + k * VEC);
+}
+
+// The same two loads from shared memory (plain loads; the staged kernel reads its own buffers).
+template <int P, int LSC>
+__device__ __forceinline__ void load_spinor_smem(const char* site_block, int s, typename Store<P>::R* psi) {
+  constexpr int VEC = Store<P>::VEC;
+  constexpr int NCH = 24 / VEC;
+  const char* b = site_block + (size_t)s * 16;
+#pragma unroll
+  for (int k = 0; k < NCH; ++k) ld16c<P>(b + (size_t)k * LSC * 16, psi + k * VEC);
+}
+
+template <int P, bool C12>
+__device__ __forceinline__ void load_link_smem(const char* p, typename Store<P>::R* u) {
+  using R = typename Store<P>::R;
+  constexpr int VEC = Store<P>::VEC;
+  constexpr int NR = C12 ? 12 : 18;
+  constexpr int NV = (NR + VEC - 1) / VEC;
+  R buf[NV * VEC];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) ld16c<P>(p + v * 16, buf + v * VEC);
+#pragma unroll
+  for (int i = 0; i < NR; ++i) u[i] = buf[i];
+  if (C12) reconstruct_row2(u);
 }
 
 // (Mooee aux)_s or (Mooee^+ aux)_s for one slice: the upper (P+) reals couple to s-1 and the
