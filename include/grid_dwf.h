@@ -26,10 +26,13 @@
  *      spinor  [t][z][y][x][s][spin 4][colour 3]        (x fastest among the 4D coordinates),
  *      gauge   [t][z][y][x][mu 4][a 3][b 3]              (row a, column b of U_mu(x)).
  *  - Device field layout (what dhop/mooee/mpc/... read and write): a half field of one parity
- *    holds V/2 checkerboard sites (cb index = lexicographic 4D index / 2); each site is one
- *    contiguous block of Ls * 24 reals stored as [chunk][s][16 bytes], chunk = 24 reals / (16
- *    bytes / sizeof(real)). A full field is the even half followed by the odd half.
- *    grid_dwf_field_bytes gives the sizes; grid_dwf_pack/unpack convert from/to canonical.
+ *    holds V/2 checkerboard sites (cb index = lexicographic 4D index / 2). The fifth dimension
+ *    is padded to Lsp = Ls rounded up to even (the pad slice is zero) and stored in slice pairs:
+ *    each site is one contiguous block of Lsp * 24 reals made of 16-byte vectors ordered
+ *    [chunk k][pair q], vector (k, q) holding reals RV*k .. RV*k+RV-1 of slices 2q and 2q+1,
+ *    real-major (RV = 1, 2, 4 for FP64, FP32, FP16/BF16). A full field is the even half followed
+ *    by the odd half. grid_dwf_field_bytes gives the sizes; grid_dwf_pack/unpack convert
+ *    from/to canonical.
  *  - Precisions: GRID_DWF_FP64 (double storage and arithmetic), GRID_DWF_FP32 (float),
  *    GRID_DWF_FP16 and GRID_DWF_BF16 (half / bfloat16 storage, float arithmetic).
  *  - Aliasing: output buffers may not overlap inputs (GRID_DWF_ERR_ALIAS), except where a call
@@ -89,7 +92,7 @@ int grid_dwf_set_stream(grid_dwf_t* h, void* stream);
 const char* grid_dwf_last_error(const grid_dwf_t* h);
 const char* grid_dwf_status_string(int code);
 
-/* Bytes of a device field of the given precision and subset (half: V/2*Ls*24 reals). */
+/* Bytes of a device field of the given precision and subset (half: V/2 * Lsp * 24 reals). */
 int grid_dwf_field_bytes(const grid_dwf_t* h, int precision, int subset, size_t* bytes);
 
 /* Upload the links. U is the canonical FP64 gauge field (host or device pointer; the library
@@ -150,12 +153,14 @@ int grid_dwf_force(grid_dwf_t* h, int precision, const void* psi, void* chi, dou
  * library's device image, present on every GPU that loads the library until the process exits.
  * The paper has no counterpart; this is a service of the library.
  *   a, b      device fields of `precision` in the device layout (16-byte aligned), nsites
- *             checkerboard site blocks of Ls slices each (V/2 for a half field, V for a full one);
+ *             checkerboard site blocks of Ls slices each, padded to even as in every field of
+ *             this library (V/2 site blocks for a half field, V for a full one);
  *   result    device pointer to 2 doubles (8-byte aligned), receives (re, im) (im = 0 for |a|^2);
  *   stream    cudaStream_t the two kernels run on (NULL = legacy default stream); asynchronous;
  *   err       optional buffer for a message on failure.
- * Limit: nsites * Ls <= 11184810 five-dimensional sites (e.g. a 32^4 x 16 half field, 8388608);
- * larger fields are rejected with GRID_DWF_ERR_INVALID_ARG before anything runs. The first call
+ * Limit: nsites * Lsp <= 22369620 five-dimensional sites, Lsp = Ls rounded up to even (e.g. a
+ * 32^4 x 16 full field, 16777216); larger fields are rejected with GRID_DWF_ERR_INVALID_ARG
+ * before anything runs. The first call
  * on a device looks up the array's device address (once per device, with that device current);
  * make that first call before any stream capture. All calls share the one array, which keeps the
  * last call's partial sums (each call overwrites what it reads), so calls whose kernels overlap

@@ -86,7 +86,10 @@ int cuda_fail(grid_dwf_t* h, cudaError_t e, const char* where) {
 
 bool valid_prec(int p) { return p >= GRID_DWF_FP64 && p <= GRID_DWF_BF16; }
 
-size_t half_bytes(const grid_dwf_t* h, int prec) { return (size_t)h->g.N4h * h->Ls * 24 * prec_bytes(prec); }
+// A half field: V/2 site blocks of the padded Ls x 24 reals.
+size_t half_bytes(const grid_dwf_t* h, int prec) {
+  return (size_t)h->g.N4h * ls_padded(h->Ls) * 24 * prec_bytes(prec);
+}
 
 size_t subset_bytes(const grid_dwf_t* h, int prec, int subset) {
   return half_bytes(h, prec) * (subset == GRID_DWF_FULL ? 2 : 1);
@@ -141,8 +144,6 @@ int ensure_gauge(grid_dwf_t* h, int prec) {
   return GRID_DWF_OK;
 }
 
-int choose_st(int prec, int Ls) { return dhop_slices_per_thread(prec, dhop_ls_specialised(Ls) ? Ls : 0); }
-
 // One half-lattice hopping application with its fused epilogue.
 int dhop_half(grid_dwf_t* h, int prec, const void* in, void* out, int out_parity, bool dag, int pre, int post,
               double alpha, double beta, const void* aux) {
@@ -155,8 +156,7 @@ int dhop_half(grid_dwf_t* h, int prec, const void* in, void* out, int out_parity
   a.Uin = h->gauge[prec][1 - out_parity];
   a.g = h->g;
   a.out_parity = out_parity;
-  const int st = choose_st(prec, h->Ls);
-  a.nsg = h->Ls / st;
+  a.nsg = dhop_threads_per_site(prec, h->Ls);
   a.sites_per_cta = 128 / a.nsg;
   if (a.sites_per_cta < 1) a.sites_per_cta = 1;
   a.pre = pre;
@@ -171,7 +171,9 @@ int dhop_half(grid_dwf_t* h, int prec, const void* in, void* out, int out_parity
   int threads = a.nsg * a.sites_per_cta;
   int blocks = (h->g.N4h + a.sites_per_cta - 1) / a.sites_per_cta;
   const size_t rbytes = prec == GRID_DWF_FP64 ? 8 : 4;
-  size_t smem = post != POST_NONE ? (size_t)a.sites_per_cta * h->Ls * 24 * rbytes : 0;
+  size_t smem = (dhop_stage_links(prec) ? dhop_link_smem_bytes(a.sites_per_cta, link_bytes(prec_bytes(prec), h->c12))
+                                        : 0) +
+                (post != POST_NONE ? (size_t)a.sites_per_cta * h->Ls * 24 * rbytes : 0);
   // Staged (bulk-copy) kernel for the bandwidth-bound precisions when a row segment fits.
   a.seg = 0;
   if (h->staged && prec != GRID_DWF_FP64 && dhop_ls_specialised(h->Ls)) {
@@ -179,16 +181,16 @@ int dhop_half(grid_dwf_t* h, int prec, const void* in, void* out, int out_parity
     a.seg = tma_choose_seg(h->g.Lxh, h->Ls, prec_bytes(prec), h->c12, post_site);
   }
   if (a.seg > 0) {
-    threads = a.seg * h->Ls;
+    threads = a.seg * ls_half(h->Ls);
     blocks = h->g.N4h / a.seg;
     smem = tma_plan(a.seg, h->Ls, prec_bytes(prec), link_bytes(prec_bytes(prec), h->c12)).bytes;
   }
   cudaError_t e;
   switch (prec) {
-    case GRID_DWF_FP64: e = launch_dhop<P64>(a, st, dag, h->c12, threads, blocks, smem, h->stream); break;
-    case GRID_DWF_FP32: e = launch_dhop<P32>(a, st, dag, h->c12, threads, blocks, smem, h->stream); break;
-    case GRID_DWF_FP16: e = launch_dhop<P16>(a, st, dag, h->c12, threads, blocks, smem, h->stream); break;
-    default: e = launch_dhop<PB16>(a, st, dag, h->c12, threads, blocks, smem, h->stream); break;
+    case GRID_DWF_FP64: e = launch_dhop<P64>(a, dag, h->c12, threads, blocks, smem, h->stream); break;
+    case GRID_DWF_FP32: e = launch_dhop<P32>(a, dag, h->c12, threads, blocks, smem, h->stream); break;
+    case GRID_DWF_FP16: e = launch_dhop<P16>(a, dag, h->c12, threads, blocks, smem, h->stream); break;
+    default: e = launch_dhop<PB16>(a, dag, h->c12, threads, blocks, smem, h->stream); break;
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "dhop launch");
   return GRID_DWF_OK;

@@ -4,9 +4,9 @@
 
 namespace gdwf {
 
-template <int ST, bool DAG, bool C12, int LSC>
+template <bool DAG, bool C12, int LSC>
 static cudaError_t launch_one(const DhopArgs& a, int threads, int blocks, size_t smem, cudaStream_t stream) {
-  auto kern = dhop_kernel<DWF_PREC, ST, DAG, C12, LSC>;
+  auto kern = dhop_kernel<DWF_PREC, DAG, C12, LSC>;
   if (smem > 48 * 1024) {
     static size_t configured = 0;  // per instantiation
     if (smem > configured) {
@@ -35,7 +35,6 @@ static cudaError_t launch_tma(const DhopArgs& a, int threads, int blocks, size_t
 template <int LSC>
 static cudaError_t launch_ls(const DhopArgs& a, bool dag, bool c12, int threads, int blocks, size_t smem,
                              cudaStream_t stream) {
-  constexpr int ST = dhop_slices_per_thread(DWF_PREC, LSC);
   if constexpr (LSC > 0 && DWF_PREC != P64) {
     if (a.seg > 0) {
       if (dag) return c12 ? launch_tma<true, true, LSC>(a, threads, blocks, smem, stream)
@@ -44,17 +43,15 @@ static cudaError_t launch_ls(const DhopArgs& a, bool dag, bool c12, int threads,
                  : launch_tma<false, false, LSC>(a, threads, blocks, smem, stream);
     }
   }
-  if (dag) return c12 ? launch_one<ST, true, true, LSC>(a, threads, blocks, smem, stream)
-                      : launch_one<ST, true, false, LSC>(a, threads, blocks, smem, stream);
-  return c12 ? launch_one<ST, false, true, LSC>(a, threads, blocks, smem, stream)
-             : launch_one<ST, false, false, LSC>(a, threads, blocks, smem, stream);
+  if (dag) return c12 ? launch_one<true, true, LSC>(a, threads, blocks, smem, stream)
+                      : launch_one<true, false, LSC>(a, threads, blocks, smem, stream);
+  return c12 ? launch_one<false, true, LSC>(a, threads, blocks, smem, stream)
+             : launch_one<false, false, LSC>(a, threads, blocks, smem, stream);
 }
 
 template <>
-cudaError_t launch_dhop<DWF_PREC>(const DhopArgs& a, int st, bool dag, bool c12, int threads, int blocks, size_t smem,
+cudaError_t launch_dhop<DWF_PREC>(const DhopArgs& a, bool dag, bool c12, int threads, int blocks, size_t smem,
                                   cudaStream_t stream) {
-  if (a.seg == 0 && st != dhop_slices_per_thread(DWF_PREC, dhop_ls_specialised(a.g.Ls) ? a.g.Ls : 0))
-    return cudaErrorInvalidValue;
   switch (a.g.Ls) {
 #define DWF_CASE(L_) \
   case L_:           \

@@ -12,11 +12,13 @@
 // as "project to a half spinor, multiply by the link, reconstruct", so that each hop costs two
 // colour mat-vecs instead of four.
 //
-// Thread mapping: one thread per (4D checkerboard site, s-group); a site's Ls slices are split
-// into nsg = Ls / ST groups and thread sg handles s = sg, sg + nsg, ..., so that the lanes of a
-// warp read consecutive 16-byte vectors of the neighbour's site block. All threads of a site
-// load the same link (a broadcast load), so every link is read from memory once per site and
-// reused for all Ls slices; a CTA holds whole sites, which the fused Mooee^-1 epilogue needs.
+// Thread mapping. FP32 and the 16-bit storage formats: one thread per (4D checkerboard site,
+// slice pair); every real of the two slices is a float2 and each hop (projection, SU(3)
+// product, reconstruction) runs on packed two-wide FP32 instructions, one instruction for two
+// slices. FP64: one thread per (site, slice) with scalar arithmetic (the FP64 pipe, not the
+// instruction issue, bounds it). All threads of a site load the same link (a broadcast load), so
+// every link is read from memory once per site and reused for all Ls slices; a CTA holds whole
+// sites, which the fused Mooee^-1 epilogue needs.
 //
 // Epilogue (all optional, chosen per launch):
 //   out = post( alpha * Dhop_in + beta * pre(aux) ),
@@ -41,7 +43,7 @@ struct DhopArgs {
   const void* Uin;   // links of the input-parity sites (backward hops)
   Geom g;
   int out_parity;
-  int nsg;            // s-groups per site
+  int nsg;            // threads per site (slice pairs, or slices in FP64)
   int sites_per_cta;  // whole sites per CTA
   int pre, post;
   double alpha, beta;
@@ -210,36 +212,7 @@ __device__ __forceinline__ void load_link(const char* p, typename Store<P>::R* u
   if (C12) reconstruct_row2(u);
 }
 
-template <int P, int LSC = 0>
-__device__ __forceinline__ void load_spinor(const char* site_block, int s, int Ls_rt, typename Store<P>::R* psi) {
-  constexpr int VEC = Store<P>::VEC;
-  constexpr int NCH = 24 / VEC;
-  const int Ls = LSC > 0 ? LSC : Ls_rt;
-  const char* b = site_block + (size_t)s * 16;
-#pragma unroll
-  for (int k = 0; k < NCH; ++k) ld16<P>(b + (size_t)k * Ls * 16, psi + k * VEC);
-}
-
-template <int P, int LSC = 0>
-__device__ __forceinline__ void store_spinor(char* site_block, int s, int Ls_rt, const typename Store<P>::R* v) {
-  constexpr int VEC = Store<P>::VEC;
-  constexpr int NCH = 24 / VEC;
-  const int Ls = LSC > 0 ? LSC : Ls_rt;
-  char* b = site_block + (size_t)s * 16;
-#pragma unroll
-  for (int k = 0; k < NCH; ++k) st16<P>(b + (size_t)k * Ls * 16, v + k * VEC);
-}
-
-// The same two loads from shared memory (plain loads; the staged kernel reads its own buffers).
-template <int P, int LSC>
-__device__ __forceinline__ void load_spinor_smem(const char* site_block, int s, typename Store<P>::R* psi) {
-  constexpr int VEC = Store<P>::VEC;
-  constexpr int NCH = 24 / VEC;
-  const char* b = site_block + (size_t)s * 16;
-#pragma unroll
-  for (int k = 0; k < NCH; ++k) ld16c<P>(b + (size_t)k * LSC * 16, psi + k * VEC);
-}
-
+// A link from shared memory (plain loads; the staged kernel reads its own buffers).
 template <int P, bool C12>
 __device__ __forceinline__ void load_link_smem(const char* p, typename Store<P>::R* u) {
   using R = typename Store<P>::R;
@@ -254,36 +227,244 @@ __device__ __forceinline__ void load_link_smem(const char* p, typename Store<P>:
   if (C12) reconstruct_row2(u);
 }
 
-// (Mooee aux)_s or (Mooee^+ aux)_s for one slice: the upper (P+) reals couple to s-1 and the
-// lower (P-) reals to s+1, with +m replacing -1 on the wrap-around; the adjoint swaps them.
+// Copy one stored link (whole 16-byte vectors) from global to shared memory.
+template <int P, bool C12>
+__device__ __forceinline__ void copy_link(char* dst, const char* src) {
+  constexpr int LB = link_bytes(sizeof(typename Store<P>::T), C12);
+#pragma unroll
+  for (int v = 0; v < LB / 16; ++v)
+    *reinterpret_cast<uint4*>(dst + v * 16) = __ldg(reinterpret_cast<const uint4*>(src + v * 16));
+}
+
+// Whether the direct kernel stages each site's eight links in shared memory (FP32, FP64: the
+// broadcast link loads of all slice pairs cost more than the staging), or reads them directly
+// (FP16/BF16: 48-byte links, measured faster without staging).
+__host__ __device__ constexpr bool dhop_stage_links(int prec) { return prec == P32 || prec == P64; }
+
+// Shared memory of the staged links of one CTA (8 links per site), a multiple of 16 bytes.
+__host__ __device__ constexpr size_t dhop_link_smem_bytes(int sites_per_cta, int link_b) {
+  return (size_t)sites_per_cta * 8 * link_b;
+}
+
+// ---------------------------------------------------------------- packed two-slice algebra
+// The same projection, SU(3) product and reconstruction on float2 values, .x for slice 2q and
+// .y for slice 2q+1; every operation is one packed FP32x2 instruction.
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+template <int SIG>
+__device__ __forceinline__ void project2(int mu, const float2* psi, float2* h) {
+  const float2 P1 = f2((float)SIG), M1 = f2((float)-SIG);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float2 r0 = psi[(0 * 3 + c) * 2], i0 = psi[(0 * 3 + c) * 2 + 1];
+    const float2 r1 = psi[(1 * 3 + c) * 2], i1 = psi[(1 * 3 + c) * 2 + 1];
+    const float2 r2 = psi[(2 * 3 + c) * 2], i2 = psi[(2 * 3 + c) * 2 + 1];
+    const float2 r3 = psi[(3 * 3 + c) * 2], i3 = psi[(3 * 3 + c) * 2 + 1];
+    float2 h0r, h0i, h1r, h1i;
+    if (mu == 0) {  // h0 = psi0 - SIG i psi3, h1 = psi1 - SIG i psi2
+      h0r = ffma2(P1, i3, r0);
+      h0i = ffma2(M1, r3, i0);
+      h1r = ffma2(P1, i2, r1);
+      h1i = ffma2(M1, r2, i1);
+    } else if (mu == 1) {  // h0 = psi0 - SIG psi3, h1 = psi1 + SIG psi2
+      h0r = ffma2(M1, r3, r0);
+      h0i = ffma2(M1, i3, i0);
+      h1r = ffma2(P1, r2, r1);
+      h1i = ffma2(P1, i2, i1);
+    } else if (mu == 2) {  // h0 = psi0 - SIG i psi2, h1 = psi1 + SIG i psi3
+      h0r = ffma2(P1, i2, r0);
+      h0i = ffma2(M1, r2, i0);
+      h1r = ffma2(M1, i3, r1);
+      h1i = ffma2(P1, r3, i1);
+    } else {  // h0 = psi0 + SIG psi2, h1 = psi1 + SIG psi3
+      h0r = ffma2(P1, r2, r0);
+      h0i = ffma2(P1, i2, i0);
+      h1r = ffma2(P1, r3, r1);
+      h1i = ffma2(P1, i3, i1);
+    }
+    h[(0 * 3 + c) * 2] = h0r;
+    h[(0 * 3 + c) * 2 + 1] = h0i;
+    h[(1 * 3 + c) * 2] = h1r;
+    h[(1 * 3 + c) * 2 + 1] = h1i;
+  }
+}
+
+// o = U h or U^+ h for both spins of the half spinor and both slices; u scalar row-major 3x3.
+template <bool DAGGER>
+__device__ __forceinline__ void su3_mul2(const float* u, const float2* h, float2* o) {
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float2 re, im;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const int e = DAGGER ? (b * 3 + a) : (a * 3 + b);
+        const float ur = u[e * 2];
+        const float ui = DAGGER ? -u[e * 2 + 1] : u[e * 2 + 1];
+        const float2 hr = h[(sp * 3 + b) * 2], hi = h[(sp * 3 + b) * 2 + 1];
+        if (b == 0) {
+          re = fmul2(f2(ur), hr);
+          im = fmul2(f2(ur), hi);
+        } else {
+          re = ffma2(f2(ur), hr, re);
+          im = ffma2(f2(ur), hi, im);
+        }
+        re = ffma2(f2(-ui), hi, re);
+        im = ffma2(f2(ui), hr, im);
+      }
+      o[(sp * 3 + a) * 2] = re;
+      o[(sp * 3 + a) * 2 + 1] = im;
+    }
+}
+
+// acc += c * reconstruct(uh), c = boundary phase times scale (the same for both slices).
+template <int SIG>
+__device__ __forceinline__ void accumulate2(int mu, const float2* uh, float c, float2* acc) {
+  const float2 C = f2(c), CS = f2(SIG * c), MCS = f2(-SIG * c);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float2 a0r = uh[(0 * 3 + k) * 2], a0i = uh[(0 * 3 + k) * 2 + 1];
+    const float2 a1r = uh[(1 * 3 + k) * 2], a1i = uh[(1 * 3 + k) * 2 + 1];
+    float2* s0 = acc + (0 * 3 + k) * 2;
+    float2* s1 = acc + (1 * 3 + k) * 2;
+    float2* s2 = acc + (2 * 3 + k) * 2;
+    float2* s3 = acc + (3 * 3 + k) * 2;
+    s0[0] = ffma2(C, a0r, s0[0]);
+    s0[1] = ffma2(C, a0i, s0[1]);
+    s1[0] = ffma2(C, a1r, s1[0]);
+    s1[1] = ffma2(C, a1i, s1[1]);
+    if (mu == 0) {  // spin2 += SIG i uh1, spin3 += SIG i uh0
+      s2[0] = ffma2(MCS, a1i, s2[0]);
+      s2[1] = ffma2(CS, a1r, s2[1]);
+      s3[0] = ffma2(MCS, a0i, s3[0]);
+      s3[1] = ffma2(CS, a0r, s3[1]);
+    } else if (mu == 1) {  // spin2 += SIG uh1, spin3 -= SIG uh0
+      s2[0] = ffma2(CS, a1r, s2[0]);
+      s2[1] = ffma2(CS, a1i, s2[1]);
+      s3[0] = ffma2(MCS, a0r, s3[0]);
+      s3[1] = ffma2(MCS, a0i, s3[1]);
+    } else if (mu == 2) {  // spin2 += SIG i uh0, spin3 -= SIG i uh1
+      s2[0] = ffma2(MCS, a0i, s2[0]);
+      s2[1] = ffma2(CS, a0r, s2[1]);
+      s3[0] = ffma2(CS, a1i, s3[0]);
+      s3[1] = ffma2(MCS, a1r, s3[1]);
+    } else {  // spin2 += SIG uh0, spin3 += SIG uh1
+      s2[0] = ffma2(CS, a0r, s2[0]);
+      s2[1] = ffma2(CS, a0i, s2[1]);
+      s3[0] = ffma2(CS, a1r, s3[0]);
+      s3[1] = ffma2(CS, a1i, s3[1]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- layout accessors
+// Site blocks are [chunk k][pair q] of 16-byte vectors (dwf_common.cuh). LSH > 0 fixes the
+// number of pairs at compile time, so chunk offsets become immediates.
+
+// Both slices of pair q as float2 (FP32 arithmetic; not for FP64). GLOBAL selects the
+// read-only cache path (global memory) or plain loads (shared memory).
+template <int P, int LSH, bool GLOBAL = true>
+__device__ __forceinline__ void load_pair(const char* blk, int q, int Lsh_rt, float2* v) {
+  constexpr int VEC = Store<P>::VEC, RV = Store<P>::RV, NCH = Store<P>::NCH;
+  const int Lsh = LSH > 0 ? LSH : Lsh_rt;
+  const char* b = blk + (size_t)q * 16;
+#pragma unroll
+  for (int k = 0; k < NCH; ++k) {
+    float t[VEC];
+    if (GLOBAL)
+      ld16<P>(b + (size_t)k * Lsh * 16, t);
+    else
+      ld16c<P>(b + (size_t)k * Lsh * 16, t);
+#pragma unroll
+    for (int j = 0; j < RV; ++j) v[RV * k + j] = make_float2(t[2 * j], t[2 * j + 1]);
+  }
+}
+
+template <int P, int LSH>
+__device__ __forceinline__ void store_pair(char* blk, int q, int Lsh_rt, const float2* v) {
+  constexpr int VEC = Store<P>::VEC, RV = Store<P>::RV, NCH = Store<P>::NCH;
+  const int Lsh = LSH > 0 ? LSH : Lsh_rt;
+  char* b = blk + (size_t)q * 16;
+#pragma unroll
+  for (int k = 0; k < NCH; ++k) {
+    float t[VEC];
+#pragma unroll
+    for (int j = 0; j < RV; ++j) {
+      t[2 * j] = v[RV * k + j].x;
+      t[2 * j + 1] = v[RV * k + j].y;
+    }
+    st16<P>(b + (size_t)k * Lsh * 16, t);
+  }
+}
+
+// FP64: slice s alone; real k of slice s is the double at byte k * Lsh * 16 + s * 8.
+template <int LSH, bool GLOBAL = true>
+__device__ __forceinline__ void load_lane64(const char* blk, int s, int Lsh_rt, double* v) {
+  const int Lsh = LSH > 0 ? LSH : Lsh_rt;
+  const char* b = blk + (size_t)s * 8;
+#pragma unroll
+  for (int k = 0; k < 24; ++k) {
+    const double* p = reinterpret_cast<const double*>(b + (size_t)k * Lsh * 16);
+    v[k] = GLOBAL ? __ldg(p) : *p;
+  }
+}
+
+template <int LSH>
+__device__ __forceinline__ void store_lane64(char* blk, int s, int Lsh_rt, const double* v) {
+  const int Lsh = LSH > 0 ? LSH : Lsh_rt;
+  char* b = blk + (size_t)s * 8;
+#pragma unroll
+  for (int k = 0; k < 24; ++k) *reinterpret_cast<double*>(b + (size_t)k * Lsh * 16) = v[k];
+}
+
+// Any precision: the 24 reals of slice s (the lane of its pair), in the arithmetic type.
+template <int P>
+__device__ __forceinline__ void load_slice(const char* blk, int s, int Lsh, typename Store<P>::R* v) {
+  if constexpr (P == P64) {
+    load_lane64<0>(blk, s, Lsh, v);
+  } else {
+    constexpr int VEC = Store<P>::VEC, RV = Store<P>::RV, NCH = Store<P>::NCH;
+    const int l = s & 1;
+    const char* b = blk + (size_t)(s >> 1) * 16;
+#pragma unroll
+    for (int k = 0; k < NCH; ++k) {
+      float t[VEC];
+      ld16<P>(b + (size_t)k * Lsh * 16, t);
+#pragma unroll
+      for (int j = 0; j < RV; ++j) v[RV * k + j] = t[2 * j + l];
+    }
+  }
+}
+
+// (Mooee aux)_s or (Mooee^+ aux)_s for one slice s < Ls (zero for the pad slice): the upper (P+)
+// reals couple to s-1 and the lower (P-) reals to s+1, with +m replacing -1 on the wrap-around;
+// the adjoint swaps them.
 template <int P, bool DAG5>
-__device__ __forceinline__ void mooee_slice(const char* site_block, int s, int Ls, double d5, double mass,
+__device__ __forceinline__ void mooee_slice(const char* blk, int s, int Ls, int Lsh, double d5, double mass,
                                             typename Store<P>::R* o) {
   using R = typename Store<P>::R;
-  constexpr int VEC = Store<P>::VEC;
-  constexpr int NCH = 24 / VEC;
+  if (s >= Ls) {
+#pragma unroll
+    for (int r = 0; r < 24; ++r) o[r] = 0;
+    return;
+  }
   const int sm = s > 0 ? s - 1 : Ls - 1;
   const int sp = s < Ls - 1 ? s + 1 : 0;
   const R cm = s > 0 ? R(-1) : R(mass);
   const R cp = s < Ls - 1 ? R(-1) : R(mass);
-  // upper reals use (s_up, c_up), lower reals use (s_lo, c_lo)
   const int s_up = DAG5 ? sp : sm, s_lo = DAG5 ? sm : sp;
   const R c_up = DAG5 ? cp : cm, c_lo = DAG5 ? cm : cp;
   const R d = R(d5);
+  R self[24], up[24], lo[24];
+  load_slice<P>(blk, s, Lsh, self);
+  load_slice<P>(blk, s_up, Lsh, up);
+  load_slice<P>(blk, s_lo, Lsh, lo);
 #pragma unroll
-  for (int k = 0; k < NCH; ++k) {
-    R self[VEC], up[VEC], lo[VEC];
-    ld16<P>(site_block + ((size_t)k * Ls + s) * 16, self);
-    const bool need_up = k * VEC < 12;
-    const bool need_lo = (k + 1) * VEC > 12;
-    if (need_up) ld16<P>(site_block + ((size_t)k * Ls + s_up) * 16, up);
-    if (need_lo) ld16<P>(site_block + ((size_t)k * Ls + s_lo) * 16, lo);
-#pragma unroll
-    for (int v = 0; v < VEC; ++v) {
-      const int r = k * VEC + v;
-      o[r] = d * self[v] + (r < 12 ? c_up * up[v] : c_lo * lo[v]);
-    }
-  }
+  for (int r = 0; r < 24; ++r) o[r] = d * self[r] + (r < 12 ? c_up * up[r] : c_lo * lo[r]);
 }
 
 // In-place inverse of the fifth-dimension matrix along one real component of one site, held
@@ -313,107 +494,136 @@ __device__ __forceinline__ void mooee_inv_line(R* v, int Ls, bool forward_form, 
   }
 }
 
-template <int P, int ST, bool DAG, bool C12, int LSC>
-__device__ __forceinline__ void dhop_body(const DhopArgs& a) {
+// ---------------------------------------------------------------- kernel bodies
+
+// FP32 / FP16 / BF16: one thread per (site, slice pair), packed two-wide arithmetic.
+template <int P, bool DAG, bool C12, int LSC>
+__device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
   using T = typename Store<P>::T;
-  using R = typename Store<P>::R;
   constexpr int LB = link_bytes(sizeof(T), C12);
   constexpr int SF = DAG ? +1 : -1;  // forward projector (1 + SF gamma)
   constexpr int SB = -SF;            // backward projector
+  constexpr int LSHC = LSC > 0 ? ls_half(LSC) : 0;
   const int Ls = LSC > 0 ? LSC : a.g.Ls;
-  const int nsg = LSC > 0 ? LSC / ST : a.nsg;
+  const int Lsh = LSC > 0 ? LSHC : ls_half(a.g.Ls);
   const int tid = threadIdx.x;
-  const int site_local = tid / nsg;
-  const int sg = tid - site_local * nsg;
+  const int site_local = tid / Lsh;
+  const int q = tid - site_local * Lsh;
   const int site = blockIdx.x * a.sites_per_cta + site_local;
   const bool active = site_local < a.sites_per_cta && site < a.g.N4h;
-  const size_t site_bytes = (size_t)Ls * 24 * sizeof(T);
-  const R alpha = R(a.alpha);
+  const size_t site_bytes = (size_t)Lsh * 2 * 24 * sizeof(T);
+  const float alpha = (float)a.alpha;
 
-  R acc[ST][24];
+  float2 acc[24];
 #pragma unroll
-  for (int k = 0; k < ST; ++k)
-#pragma unroll
-    for (int r = 0; r < 24; ++r) acc[k][r] = 0;
+  for (int r = 0; r < 24; ++r) acc[r] = make_float2(0.f, 0.f);
+
+  // The eight links of each site, staged once per CTA: thread q of a site fetches the links of
+  // hops q, q + Lsh, ... (hop h = 2 mu + backward), so every link is requested from memory once
+  // instead of once per slice pair; the hops then read them from shared memory.
+  constexpr bool STAGE = dhop_stage_links(P);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  char* lsm = reinterpret_cast<char*>(smem_raw);  // [site_local][hop 8][LB]
+  const char* Uo = static_cast<const char*>(a.Uout);
+  const char* Ui = static_cast<const char*>(a.Uin);
+  int c[4];
+  if (active) cb_coords(a.g, site, a.out_parity, c);
+  if (STAGE) {
+    if (active) {
+      for (int h = q; h < 8; h += Lsh) {
+        const int mu = h >> 1;
+        const char* src;
+        if ((h & 1) == 0) {
+          src = Uo + ((size_t)site * 4 + mu) * LB;
+        } else {
+          int ph;
+          src = Ui + ((size_t)cb_neighbour(a.g, site, c, mu, false, ph) * 4 + mu) * LB;
+        }
+        copy_link<P, C12>(lsm + ((size_t)site_local * 8 + h) * LB, src);
+      }
+    }
+    __syncthreads();
+  }
 
   if (active) {
-    int c[4];
-    cb_coords(a.g, site, a.out_parity, c);
     const char* in = static_cast<const char*>(a.in);
-    const char* Uo = static_cast<const char*>(a.Uout);
-    const char* Ui = static_cast<const char*>(a.Uin);
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
       {  // forward hop: (1 + SF gamma_mu) U_mu(x) psi(x + mu)
         int ph;
         const int j = cb_neighbour(a.g, site, c, mu, true, ph);
-        R u[18];
-        load_link<P, C12>(Uo + ((size_t)site * 4 + mu) * LB, u);
-        const char* pj = in + (size_t)j * site_bytes;
-        const R scale = ph < 0 ? -alpha : alpha;
-#pragma unroll
-        for (int k = 0; k < ST; ++k) {
-          R psi[24], h[12], uh[12];
-          load_spinor<P, LSC>(pj, sg + k * nsg, Ls, psi);
-          project<SF>(mu, psi, h);
-          su3_mul<false>(u, h, uh);
-          accumulate<SF>(mu, uh, scale, acc[k]);
-        }
+        float u[18];
+        if (STAGE)
+          load_link_smem<P, C12>(lsm + ((size_t)site_local * 8 + 2 * mu) * LB, u);
+        else
+          load_link<P, C12>(Uo + ((size_t)site * 4 + mu) * LB, u);
+        float2 psi[24], h[12], uh[12];
+        load_pair<P, LSHC>(in + (size_t)j * site_bytes, q, Lsh, psi);
+        project2<SF>(mu, psi, h);
+        su3_mul2<false>(u, h, uh);
+        accumulate2<SF>(mu, uh, ph < 0 ? -alpha : alpha, acc);
       }
       {  // backward hop: (1 + SB gamma_mu) U_mu(x - mu)^+ psi(x - mu)
         int ph;
         const int j = cb_neighbour(a.g, site, c, mu, false, ph);
-        R u[18];
-        load_link<P, C12>(Ui + ((size_t)j * 4 + mu) * LB, u);
-        const char* pj = in + (size_t)j * site_bytes;
-        const R scale = ph < 0 ? -alpha : alpha;
-#pragma unroll
-        for (int k = 0; k < ST; ++k) {
-          R psi[24], h[12], uh[12];
-          load_spinor<P, LSC>(pj, sg + k * nsg, Ls, psi);
-          project<SB>(mu, psi, h);
-          su3_mul<true>(u, h, uh);
-          accumulate<SB>(mu, uh, scale, acc[k]);
-        }
+        float u[18];
+        if (STAGE)
+          load_link_smem<P, C12>(lsm + ((size_t)site_local * 8 + 2 * mu + 1) * LB, u);
+        else
+          load_link<P, C12>(Ui + ((size_t)j * 4 + mu) * LB, u);
+        float2 psi[24], h[12], uh[12];
+        load_pair<P, LSHC>(in + (size_t)j * site_bytes, q, Lsh, psi);
+        project2<SB>(mu, psi, h);
+        su3_mul2<true>(u, h, uh);
+        accumulate2<SB>(mu, uh, ph < 0 ? -alpha : alpha, acc);
       }
     }
   }
 
   // ------------------------------------------------------------ epilogue
-  const R beta = R(a.beta);
-  const char* auxb = a.pre != PRE_NONE ? static_cast<const char*>(a.aux) + (size_t)site * site_bytes : nullptr;
   char* outb = static_cast<char*>(a.out) + (size_t)site * site_bytes;
   if (active && a.pre != PRE_NONE) {
+    const char* auxb = static_cast<const char*>(a.aux) + (size_t)site * site_bytes;
+    const float2 B = f2((float)a.beta);
+    if (a.pre == PRE_AUX) {
+      float2 o[24];
+      load_pair<P, LSHC>(auxb, q, Lsh, o);
 #pragma unroll
-    for (int k = 0; k < ST; ++k) {
-      const int s = sg + k * nsg;
-      R o[24];
-      if (a.pre == PRE_AUX)
-        load_spinor<P, LSC>(auxb, s, Ls, o);
-      else if (a.pre == PRE_MOOEE)
-        mooee_slice<P, false>(auxb, s, Ls, a.d5, a.mass, o);
-      else
-        mooee_slice<P, true>(auxb, s, Ls, a.d5, a.mass, o);
+      for (int r = 0; r < 24; ++r) acc[r] = ffma2(B, o[r], acc[r]);
+    } else {
+      float o0[24], o1[24];
+      if (a.pre == PRE_MOOEE) {
+        mooee_slice<P, false>(auxb, 2 * q, Ls, Lsh, a.d5, a.mass, o0);
+        mooee_slice<P, false>(auxb, 2 * q + 1, Ls, Lsh, a.d5, a.mass, o1);
+      } else {
+        mooee_slice<P, true>(auxb, 2 * q, Ls, Lsh, a.d5, a.mass, o0);
+        mooee_slice<P, true>(auxb, 2 * q + 1, Ls, Lsh, a.d5, a.mass, o1);
+      }
 #pragma unroll
-      for (int r = 0; r < 24; ++r) acc[k][r] = fma_r(beta, o[r], acc[k][r]);
+      for (int r = 0; r < 24; ++r) acc[r] = ffma2(B, make_float2(o0[r], o1[r]), acc[r]);
     }
   }
+  const bool pad_lane = (Ls & 1) && q == Lsh - 1;  // slice 2q+1 is the zero pad
   if (a.post == POST_NONE) {
     if (active) {
+      if (pad_lane) {
 #pragma unroll
-      for (int k = 0; k < ST; ++k) store_spinor<P, LSC>(outb, sg + k * nsg, Ls, acc[k]);
+        for (int r = 0; r < 24; ++r) acc[r].y = 0.f;
+      }
+      store_pair<P, LSHC>(outb, q, Lsh, acc);
     }
     return;
   }
-  // Fifth-dimension inverse through shared memory: whole sites live in this CTA.
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* sm = reinterpret_cast<R*>(smem_raw);
+  // Fifth-dimension inverse through shared memory (after the staged links): whole sites live in
+  // this CTA.
+  float* sm = reinterpret_cast<float*>(smem_raw + (STAGE ? dhop_link_smem_bytes(a.sites_per_cta, LB) : 0));
   if (active) {
+    float* d0 = sm + ((size_t)site_local * Ls + 2 * q) * 24;
 #pragma unroll
-    for (int k = 0; k < ST; ++k) {
-      R* dst = sm + ((size_t)site_local * Ls + sg + k * nsg) * 24;
+    for (int r = 0; r < 24; ++r) d0[r] = acc[r].x;
+    if (!pad_lane) {
 #pragma unroll
-      for (int r = 0; r < 24; ++r) dst[r] = acc[k][r];
+      for (int r = 0; r < 24; ++r) d0[24 + r] = acc[r].y;
     }
   }
   __syncthreads();
@@ -424,52 +634,174 @@ __device__ __forceinline__ void dhop_body(const DhopArgs& a) {
     const int r = task - sl * 24;
     const bool upper = r < 12;
     const bool forward_form = (a.post == POST_INV) ? upper : !upper;
-    mooee_inv_line<R>(sm + (size_t)sl * Ls * 24 + r, Ls, forward_form, R(a.mass), R(a.inv_d5), R(a.inv_den));
+    mooee_inv_line<float>(sm + (size_t)sl * Ls * 24 + r, Ls, forward_form, (float)a.mass, (float)a.inv_d5,
+                          (float)a.inv_den);
   }
   __syncthreads();
   if (active) {
+    const float* s0 = sm + ((size_t)site_local * Ls + 2 * q) * 24;
 #pragma unroll
-    for (int k = 0; k < ST; ++k) {
-      const int s = sg + k * nsg;
-      store_spinor<P, LSC>(outb, s, Ls, sm + ((size_t)site_local * Ls + s) * 24);
+    for (int r = 0; r < 24; ++r) acc[r] = make_float2(s0[r], pad_lane ? 0.f : s0[24 + r]);
+    store_pair<P, LSHC>(outb, q, Lsh, acc);
+  }
+}
+
+// FP64: one thread per (site, slice), scalar arithmetic.
+template <bool DAG, bool C12, int LSC>
+__device__ __forceinline__ void dhop_body_lane64(const DhopArgs& a) {
+  constexpr int LB = link_bytes(8, C12);
+  constexpr int SF = DAG ? +1 : -1;
+  constexpr int SB = -SF;
+  constexpr int LSHC = LSC > 0 ? ls_half(LSC) : 0;
+  const int Ls = LSC > 0 ? LSC : a.g.Ls;
+  const int Lsh = LSC > 0 ? LSHC : ls_half(a.g.Ls);
+  const int Lsp = 2 * Lsh;
+  const int tid = threadIdx.x;
+  const int site_local = tid / Lsp;
+  const int s = tid - site_local * Lsp;
+  const int site = blockIdx.x * a.sites_per_cta + site_local;
+  const bool active = site_local < a.sites_per_cta && site < a.g.N4h;
+  const size_t site_bytes = (size_t)Lsp * 24 * 8;
+  const double alpha = a.alpha;
+
+  double acc[24];
+#pragma unroll
+  for (int r = 0; r < 24; ++r) acc[r] = 0;
+  // links staged once per CTA, as in dhop_body_pair
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  char* lsm = reinterpret_cast<char*>(smem_raw);  // [site_local][hop 8][LB]
+  int c[4];
+  if (active) {
+    cb_coords(a.g, site, a.out_parity, c);
+    const char* Uo = static_cast<const char*>(a.Uout);
+    const char* Ui = static_cast<const char*>(a.Uin);
+    for (int h = s; h < 8; h += Lsp) {
+      const int mu = h >> 1;
+      const char* src;
+      if ((h & 1) == 0) {
+        src = Uo + ((size_t)site * 4 + mu) * LB;
+      } else {
+        int ph;
+        src = Ui + ((size_t)cb_neighbour(a.g, site, c, mu, false, ph) * 4 + mu) * LB;
+      }
+      copy_link<P64, C12>(lsm + ((size_t)site_local * 8 + h) * LB, src);
     }
+  }
+  __syncthreads();
+  if (active) {
+    const char* in = static_cast<const char*>(a.in);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      {
+        int ph;
+        const int j = cb_neighbour(a.g, site, c, mu, true, ph);
+        double u[18], psi[24], h[12], uh[12];
+        load_link_smem<P64, C12>(lsm + ((size_t)site_local * 8 + 2 * mu) * LB, u);
+        load_lane64<LSHC>(in + (size_t)j * site_bytes, s, Lsh, psi);
+        project<SF>(mu, psi, h);
+        su3_mul<false>(u, h, uh);
+        accumulate<SF>(mu, uh, ph < 0 ? -alpha : alpha, acc);
+      }
+      {
+        int ph;
+        const int j = cb_neighbour(a.g, site, c, mu, false, ph);
+        double u[18], psi[24], h[12], uh[12];
+        load_link_smem<P64, C12>(lsm + ((size_t)site_local * 8 + 2 * mu + 1) * LB, u);
+        load_lane64<LSHC>(in + (size_t)j * site_bytes, s, Lsh, psi);
+        project<SB>(mu, psi, h);
+        su3_mul<true>(u, h, uh);
+        accumulate<SB>(mu, uh, ph < 0 ? -alpha : alpha, acc);
+      }
+    }
+  }
+  char* outb = static_cast<char*>(a.out) + (size_t)site * site_bytes;
+  if (active && a.pre != PRE_NONE) {
+    const char* auxb = static_cast<const char*>(a.aux) + (size_t)site * site_bytes;
+    double o[24];
+    if (a.pre == PRE_AUX)
+      load_lane64<LSHC>(auxb, s, Lsh, o);
+    else if (a.pre == PRE_MOOEE)
+      mooee_slice<P64, false>(auxb, s, Ls, Lsh, a.d5, a.mass, o);
+    else
+      mooee_slice<P64, true>(auxb, s, Ls, Lsh, a.d5, a.mass, o);
+#pragma unroll
+    for (int r = 0; r < 24; ++r) acc[r] = fma(a.beta, o[r], acc[r]);
+  }
+  const bool pad = s >= Ls;
+  if (a.post == POST_NONE) {
+    if (active) {
+      if (pad) {
+#pragma unroll
+        for (int r = 0; r < 24; ++r) acc[r] = 0;
+      }
+      store_lane64<LSHC>(outb, s, Lsh, acc);
+    }
+    return;
+  }
+  double* sm = reinterpret_cast<double*>(smem_raw + dhop_link_smem_bytes(a.sites_per_cta, LB));
+  if (active && !pad) {
+    double* dst = sm + ((size_t)site_local * Ls + s) * 24;
+#pragma unroll
+    for (int r = 0; r < 24; ++r) dst[r] = acc[r];
+  }
+  __syncthreads();
+  const int first_site = blockIdx.x * a.sites_per_cta;
+  const int nsites = min(a.sites_per_cta, a.g.N4h - first_site);
+  for (int task = tid; task < nsites * 24; task += blockDim.x) {
+    const int sl = task / 24;
+    const int r = task - sl * 24;
+    const bool upper = r < 12;
+    const bool forward_form = (a.post == POST_INV) ? upper : !upper;
+    mooee_inv_line<double>(sm + (size_t)sl * Ls * 24 + r, Ls, forward_form, a.mass, a.inv_d5, a.inv_den);
+  }
+  __syncthreads();
+  if (active) {
+    if (!pad) {
+      const double* src = sm + ((size_t)site_local * Ls + s) * 24;
+#pragma unroll
+      for (int r = 0; r < 24; ++r) acc[r] = src[r];
+    } else {
+#pragma unroll
+      for (int r = 0; r < 24; ++r) acc[r] = 0;
+    }
+    store_lane64<LSHC>(outb, s, Lsh, acc);
   }
 }
 
 // Register budget: at most 256 threads per CTA and two such CTAs per SM (128 registers per
-// thread): the measured optimum for the FP32 and 16-bit kernels on GB300 (more resident warps
-// with fewer registers spill and run slower). The FP64 kernel is bound by the FP64 pipe and
+// thread) for the packed FP32 and 16-bit kernels; the FP64 kernel is bound by the FP64 pipe and
 // keeps more registers instead.
 template <int P>
 struct DhopOccupancy {
   static constexpr int MIN_BLOCKS = (P == P64) ? 1 : 2;
 };
 
-// Slices per thread: two for the 16-bit storage formats at a compile-time Ls (halves the link
-// loads and conversions per slice), one otherwise.
-__host__ __device__ constexpr int dhop_slices_per_thread(int prec, int lsc) {
-  return (lsc > 0 && (prec == P16 || prec == PB16)) ? 2 : 1;
-}
+// Threads per site: slice pairs (packed kernels) or padded slices (FP64).
+inline int dhop_threads_per_site(int prec, int Ls) { return prec == P64 ? ls_padded(Ls) : ls_half(Ls); }
 
 // Ls values with a compile-time specialisation; any other Ls runs the generic kernel (LSC = 0).
 #define DWF_LS_SPECIALISATIONS(M) M(8) M(12) M(16) M(24) M(32)
 inline bool dhop_ls_specialised(int Ls) { return Ls == 8 || Ls == 12 || Ls == 16 || Ls == 24 || Ls == 32; }
 
-template <int P, int ST, bool DAG, bool C12, int LSC>
+template <int P, bool DAG, bool C12, int LSC>
 __global__ void __launch_bounds__(256, DhopOccupancy<P>::MIN_BLOCKS) dhop_kernel(const __grid_constant__ DhopArgs a) {
-  dhop_body<P, ST, DAG, C12, LSC>(a);
+  if constexpr (P == P64)
+    dhop_body_lane64<DAG, C12, LSC>(a);
+  else
+    dhop_body_pair<P, DAG, C12, LSC>(a);
 }
 
+// Host-side launcher, instantiated once per storage precision in its own translation unit.
 template <int P>
-cudaError_t launch_dhop(const DhopArgs& a, int st, bool dag, bool c12, int threads, int blocks, size_t smem,
+cudaError_t launch_dhop(const DhopArgs& a, bool dag, bool c12, int threads, int blocks, size_t smem,
                         cudaStream_t stream);
 template <>
-cudaError_t launch_dhop<P64>(const DhopArgs&, int, bool, bool, int, int, size_t, cudaStream_t);
+cudaError_t launch_dhop<P64>(const DhopArgs&, bool, bool, int, int, size_t, cudaStream_t);
 template <>
-cudaError_t launch_dhop<P32>(const DhopArgs&, int, bool, bool, int, int, size_t, cudaStream_t);
+cudaError_t launch_dhop<P32>(const DhopArgs&, bool, bool, int, int, size_t, cudaStream_t);
 template <>
-cudaError_t launch_dhop<P16>(const DhopArgs&, int, bool, bool, int, int, size_t, cudaStream_t);
+cudaError_t launch_dhop<P16>(const DhopArgs&, bool, bool, int, int, size_t, cudaStream_t);
 template <>
-cudaError_t launch_dhop<PB16>(const DhopArgs&, int, bool, bool, int, int, size_t, cudaStream_t);
+cudaError_t launch_dhop<PB16>(const DhopArgs&, bool, bool, int, int, size_t, cudaStream_t);
 
 }  // namespace gdwf

@@ -4,8 +4,8 @@
 // Why: in the direct kernel every thread loads its eight neighbour spinors through L1, which
 // hits only for the x hops; the other six come from L2 with ~1000-cycle latency on the two-die
 // part, and registers cannot hold enough loads in flight to cover it. Here one CTA owns a
-// segment of `seg` consecutive checkerboard sites of one x-row (all Ls slices, one thread per
-// (site, slice)). Because the cb index runs x-fastest, each neighbour row-segment is one
+// segment of `seg` consecutive checkerboard sites of one x-row (all slices, one thread per
+// (site, slice pair), packed two-wide arithmetic as in the direct kernel). Because the cb index runs x-fastest, each neighbour row-segment is one
 // contiguous run of site blocks in memory, so the CTA needs only a handful of bulk copies:
 //   x hops:            seg + 2 site blocks of the same row (x - 1 ... x + seg, wrapping),
 //   y, z, t hops:      seg site blocks of each of the six neighbour rows,
@@ -56,7 +56,7 @@ constexpr unsigned long long TMA_WAIT_LIMIT = 1ull << 24;  // try_wait rounds be
 // Shared-memory plan of one CTA (byte offsets), shared by the host launcher and the kernel.
 struct TmaPlan {
   int seg;               // sites per CTA
-  unsigned site_bytes;   // Ls * 24 * sizeof(storage)
+  unsigned site_bytes;   // padded Ls * 24 * sizeof(storage)
   unsigned lrow_bytes;   // 4 links of one site
   unsigned off_x;        // seg + 2 site blocks
   unsigned off_rows;     // 6 * seg site blocks, rows in the order y+, y-, z+, z-, t+, t-
@@ -69,7 +69,7 @@ struct TmaPlan {
 __host__ __device__ inline TmaPlan tma_plan(int seg, int Ls, int real_bytes, int link_b) {
   TmaPlan p;
   p.seg = seg;
-  p.site_bytes = (unsigned)Ls * 24u * (unsigned)real_bytes;
+  p.site_bytes = (unsigned)ls_padded(Ls) * 24u * (unsigned)real_bytes;
   p.lrow_bytes = 4u * (unsigned)link_b;
   p.off_x = 0;
   p.off_rows = p.off_x + (unsigned)(seg + 2) * p.site_bytes;
@@ -102,10 +102,10 @@ __device__ __forceinline__ unsigned copy_row_run(char* dst, const char* row_base
 template <int P, bool DAG, bool C12, int LSC>
 __device__ __forceinline__ void dhop_tma_body(const DhopArgs& a) {
   using T = typename Store<P>::T;
-  using R = typename Store<P>::R;
   constexpr int LB = link_bytes(sizeof(T), C12);
   constexpr int SF = DAG ? +1 : -1;
   constexpr int Ls = LSC;
+  constexpr int Lsh = ls_half(LSC);
   const Geom& g = a.g;
   const int seg = a.seg;
   const TmaPlan pl = tma_plan(seg, Ls, (int)sizeof(T), LB);
@@ -113,8 +113,8 @@ __device__ __forceinline__ void dhop_tma_body(const DhopArgs& a) {
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + pl.bytes - 16);
 
   const int tid = threadIdx.x;
-  const int sl = tid / Ls;  // site within the segment
-  const int s = tid - sl * Ls;
+  const int sl = tid / Lsh;  // site within the segment
+  const int q = tid - sl * Lsh;
   const int segs_per_row = g.Lxh / seg;
   const int row = blockIdx.x / segs_per_row;
   const int a0 = (blockIdx.x - row * segs_per_row) * seg;  // first xh of the segment
@@ -129,12 +129,12 @@ __device__ __forceinline__ void dhop_tma_body(const DhopArgs& a) {
   const int t = (int)r2;
   const int L1 = g.L[1], L2 = g.L[2], L3 = g.L[3];
   const int rows_pm[6] = {
-      row + (y == L1 - 1 ? -(L1 - 1) : 1),               // y+
-      row + (y == 0 ? (L1 - 1) : -1),                    // y-
-      row + (z == L2 - 1 ? -(L2 - 1) : 1) * L1,          // z+
-      row + (z == 0 ? (L2 - 1) : -1) * L1,               // z-
-      row + (t == L3 - 1 ? -(L3 - 1) : 1) * L1 * L2,     // t+
-      row + (t == 0 ? (L3 - 1) : -1) * L1 * L2,          // t-
+      row + (y == L1 - 1 ? -(L1 - 1) : 1),            // y+
+      row + (y == 0 ? (L1 - 1) : -1),                 // y-
+      row + (z == L2 - 1 ? -(L2 - 1) : 1) * L1,       // z+
+      row + (z == 0 ? (L2 - 1) : -1) * L1,            // z-
+      row + (t == L3 - 1 ? -(L3 - 1) : 1) * L1 * L2,  // t+
+      row + (t == 0 ? (L3 - 1) : -1) * L1 * L2,       // t-
   };
 
   if (tid == 0) {
@@ -148,8 +148,8 @@ __device__ __forceinline__ void dhop_tma_body(const DhopArgs& a) {
   const char* Ui = static_cast<const char*>(a.Uin);
   if (tid == 0) {
     const unsigned sb = pl.site_bytes, lr = pl.lrow_bytes;
-    unsigned total = 0;
-    total += (unsigned)(seg + 2) * sb + 6u * seg * sb + (unsigned)seg * lr + (unsigned)(seg + 2) * lr + 3u * seg * lr;
+    const unsigned total =
+        (unsigned)(seg + 2) * sb + 6u * seg * sb + (unsigned)seg * lr + (unsigned)(seg + 2) * lr + 3u * seg * lr;
     mbar_arrive_expect_tx(bar, total);
     // spinors: x range of this row, then the segment's xh range in the six neighbour rows
     copy_row_run(reinterpret_cast<char*>(smem_raw + pl.off_x), in + (size_t)row_base * sb, a0 - 1, seg + 2, g.Lxh,
@@ -174,7 +174,7 @@ __device__ __forceinline__ void dhop_tma_body(const DhopArgs& a) {
   c[2] = z;
   c[3] = t;
   c[0] = 2 * (a0 + sl) + ((a.out_parity + y + z + t) & 1);
-  const R alpha = R(a.alpha);
+  const float alpha = (float)a.alpha;
 
   bool ok = true;
   {
@@ -194,9 +194,9 @@ __device__ __forceinline__ void dhop_tma_body(const DhopArgs& a) {
     return;
   }
 
-  R acc[24];
+  float2 acc[24];
 #pragma unroll
-  for (int r = 0; r < 24; ++r) acc[r] = 0;
+  for (int r = 0; r < 24; ++r) acc[r] = make_float2(0.f, 0.f);
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu) {
 #pragma unroll
@@ -227,62 +227,84 @@ __device__ __forceinline__ void dhop_tma_body(const DhopArgs& a) {
         const int k = 2 * (mu - 1) + (fwd ? 0 : 1);
         blk = reinterpret_cast<const char*>(smem_raw + pl.off_rows + (unsigned)(k * seg + sl) * pl.site_bytes);
         lnk = fwd ? reinterpret_cast<const char*>(smem_raw + pl.off_lfwd + (unsigned)sl * pl.lrow_bytes)
-                  : reinterpret_cast<const char*>(smem_raw + pl.off_lbr + (unsigned)((mu - 1) * seg + sl) * pl.lrow_bytes);
+                  : reinterpret_cast<const char*>(smem_raw + pl.off_lbr +
+                                                  (unsigned)((mu - 1) * seg + sl) * pl.lrow_bytes);
       }
-      R u[18];
+      float u[18];
       load_link_smem<P, C12>(lnk + mu * LB, u);
-      R psi[24], h[12], uh[12];
-      load_spinor_smem<P, LSC>(blk, s, psi);
-      const R scale = ph < 0 ? -alpha : alpha;
+      float2 psi[24], h[12], uh[12];
+      load_pair<P, Lsh, false>(blk, q, Lsh, psi);
+      const float scale = ph < 0 ? -alpha : alpha;
       if (fwd) {
-        project<SF>(mu, psi, h);
-        su3_mul<false>(u, h, uh);
-        accumulate<SF>(mu, uh, scale, acc);
+        project2<SF>(mu, psi, h);
+        su3_mul2<false>(u, h, uh);
+        accumulate2<SF>(mu, uh, scale, acc);
       } else {
-        project<-SF>(mu, psi, h);
-        su3_mul<true>(u, h, uh);
-        accumulate<-SF>(mu, uh, scale, acc);
+        project2<-SF>(mu, psi, h);
+        su3_mul2<true>(u, h, uh);
+        accumulate2<-SF>(mu, uh, scale, acc);
       }
     }
   }
 
-  // ------------------------------------------------------------ epilogue (as in dhop_body)
-  const size_t gsite_bytes = (size_t)Ls * 24 * sizeof(T);
+  // ------------------------------------------------------------ epilogue (as in dhop_body_pair)
+  const size_t gsite_bytes = (size_t)Lsh * 2 * 24 * sizeof(T);
   char* outb = static_cast<char*>(a.out) + (size_t)site * gsite_bytes;
   if (a.pre != PRE_NONE) {
     const char* auxb = static_cast<const char*>(a.aux) + (size_t)site * gsite_bytes;
-    const R beta = R(a.beta);
-    R o[24];
-    if (a.pre == PRE_AUX)
-      load_spinor<P, LSC>(auxb, s, Ls, o);
-    else if (a.pre == PRE_MOOEE)
-      mooee_slice<P, false>(auxb, s, Ls, a.d5, a.mass, o);
-    else
-      mooee_slice<P, true>(auxb, s, Ls, a.d5, a.mass, o);
+    const float2 B = f2((float)a.beta);
+    if (a.pre == PRE_AUX) {
+      float2 o[24];
+      load_pair<P, Lsh>(auxb, q, Lsh, o);
 #pragma unroll
-    for (int r = 0; r < 24; ++r) acc[r] = fma_r(beta, o[r], acc[r]);
+      for (int r = 0; r < 24; ++r) acc[r] = ffma2(B, o[r], acc[r]);
+    } else {
+      float o0[24], o1[24];
+      if (a.pre == PRE_MOOEE) {
+        mooee_slice<P, false>(auxb, 2 * q, Ls, Lsh, a.d5, a.mass, o0);
+        mooee_slice<P, false>(auxb, 2 * q + 1, Ls, Lsh, a.d5, a.mass, o1);
+      } else {
+        mooee_slice<P, true>(auxb, 2 * q, Ls, Lsh, a.d5, a.mass, o0);
+        mooee_slice<P, true>(auxb, 2 * q + 1, Ls, Lsh, a.d5, a.mass, o1);
+      }
+#pragma unroll
+      for (int r = 0; r < 24; ++r) acc[r] = ffma2(B, make_float2(o0[r], o1[r]), acc[r]);
+    }
   }
+  const bool pad_lane = (Ls & 1) && q == Lsh - 1;
   if (a.post == POST_NONE) {
-    store_spinor<P, LSC>(outb, s, Ls, acc);
+    if (pad_lane) {
+#pragma unroll
+      for (int r = 0; r < 24; ++r) acc[r].y = 0.f;
+    }
+    store_pair<P, Lsh>(outb, q, Lsh, acc);
     return;
   }
   __syncthreads();  // all hops done: the staged buffers are free for the fifth-dimension solve
-  R* sm = reinterpret_cast<R*>(smem_raw);
+  float* sm = reinterpret_cast<float*>(smem_raw);
   {
-    R* dst = sm + ((size_t)sl * Ls + s) * 24;
+    float* d0 = sm + ((size_t)sl * Ls + 2 * q) * 24;
 #pragma unroll
-    for (int r = 0; r < 24; ++r) dst[r] = acc[r];
+    for (int r = 0; r < 24; ++r) d0[r] = acc[r].x;
+    if (!pad_lane) {
+#pragma unroll
+      for (int r = 0; r < 24; ++r) d0[24 + r] = acc[r].y;
+    }
   }
   __syncthreads();
   for (int task = tid; task < seg * 24; task += blockDim.x) {
-    const int q = task / 24;
-    const int r = task - q * 24;
+    const int qq = task / 24;
+    const int r = task - qq * 24;
     const bool upper = r < 12;
     const bool forward_form = (a.post == POST_INV) ? upper : !upper;
-    mooee_inv_line<R>(sm + (size_t)q * Ls * 24 + r, Ls, forward_form, R(a.mass), R(a.inv_d5), R(a.inv_den));
+    mooee_inv_line<float>(sm + (size_t)qq * Ls * 24 + r, Ls, forward_form, (float)a.mass, (float)a.inv_d5,
+                          (float)a.inv_den);
   }
   __syncthreads();
-  store_spinor<P, LSC>(outb, s, Ls, sm + ((size_t)sl * Ls + s) * 24);
+  const float* s0 = sm + ((size_t)sl * Ls + 2 * q) * 24;
+#pragma unroll
+  for (int r = 0; r < 24; ++r) acc[r] = make_float2(s0[r], pad_lane ? 0.f : s0[24 + r]);
+  store_pair<P, Lsh>(outb, q, Lsh, acc);
 }
 
 template <int P, bool DAG, bool C12, int LSC>
@@ -295,7 +317,7 @@ __global__ void __launch_bounds__(256, 2) dhop_tma_kernel(const __grid_constant_
 inline int tma_choose_seg(int lxh, int Ls, int real_bytes, bool c12, size_t post_smem_per_site) {
   const int lb = link_bytes(real_bytes, c12);
   for (int seg = 16; seg >= 4; --seg) {
-    if (lxh % seg || seg * Ls > 256) continue;
+    if (lxh % seg || seg * ls_half(Ls) > 256) continue;
     const TmaPlan p = tma_plan(seg, Ls, real_bytes, lb);
     if (p.bytes > 110 * 1024) continue;
     if (post_smem_per_site * seg > p.bytes - 16) continue;

@@ -1,13 +1,19 @@
 // Shared device-side definitions of the GB300 domain-wall operator library: storage
 // precisions, the device field layout, fast integer division and lattice geometry.
 //
-// Device spinor layout (one checkerboard half of a 5D field). For a 4D checkerboard site i
-// (cb index = lexicographic 4D index / 2, x fastest) the Ls x 24 reals of that site are one
-// contiguous block, stored as [chunk k][s][VEC reals] where each (k, s) entry is one 16-byte
-// vector: VEC = 2 (FP64), 4 (FP32), 8 (FP16/BF16) and 24/VEC chunks. Real number r of a
-// spinor is r = (spin*3 + colour)*2 + (0 re | 1 im), so chunk k holds reals k*VEC .. k*VEC+VEC-1.
-// With s innermost, the threads of one site that handle consecutive s read consecutive 16-byte
-// vectors, and every link is loaded once for all Ls slices of its site.
+// Device spinor layout (one checkerboard half of a 5D field). The fifth dimension is padded to
+// an even length Lsp = Ls + (Ls & 1) (the pad slice, if any, is always zero) and handled in
+// slice pairs (2q, 2q+1), q < Lsh = Lsp / 2. For a 4D checkerboard site i (cb index =
+// lexicographic 4D index / 2, x fastest) the Lsp x 24 reals of that site are one contiguous
+// block of 16-byte vectors ordered [chunk k][pair q]: vector (k, q) at byte (k * Lsh + q) * 16
+// holds reals RV*k .. RV*k + RV - 1 of both slices of pair q, real-major: value 2j + l is real
+// RV*k + j of slice 2q + l. RV = 1 (FP64), 2 (FP32), 4 (FP16/BF16); NCH = 24 / RV chunks.
+// Real number r of a spinor is r = (spin*3 + colour)*2 + (0 re | 1 im).
+// Why pairs: with one thread per (site, pair), every real arrives as the two slices' values
+// side by side, so the FP32 arithmetic runs as packed two-wide instructions (one instruction per
+// two slices) and each link is loaded once for two slices; consecutive threads of a site take
+// consecutive pairs, so every load is a contiguous run of whole 16-byte vectors. In FP64 the same
+// bytes read as [real k][slice s] with stride Lsp * 8 between reals.
 //
 // A full field is the even half followed by the odd half.
 //
@@ -25,6 +31,8 @@ namespace gdwf {
 
 enum Prec : int { P64 = 0, P32 = 1, P16 = 2, PB16 = 3 };
 
+// T: storage type; R: arithmetic type; VEC: values per 16-byte vector; RV = VEC / 2 reals (of
+// two slices) per vector; NCH = 24 / RV vectors per slice pair.
 template <int P>
 struct Store;
 template <>
@@ -32,28 +40,40 @@ struct Store<P64> {
   using T = double;
   using R = double;
   static constexpr int VEC = 2;
+  static constexpr int RV = 1;
+  static constexpr int NCH = 24;
 };
 template <>
 struct Store<P32> {
   using T = float;
   using R = float;
   static constexpr int VEC = 4;
+  static constexpr int RV = 2;
+  static constexpr int NCH = 12;
 };
 template <>
 struct Store<P16> {
   using T = __half;
   using R = float;
   static constexpr int VEC = 8;
+  static constexpr int RV = 4;
+  static constexpr int NCH = 6;
 };
 template <>
 struct Store<PB16> {
   using T = __nv_bfloat16;
   using R = float;
   static constexpr int VEC = 8;
+  static constexpr int RV = 4;
+  static constexpr int NCH = 6;
 };
 
 inline int prec_bytes(int p) { return p == P64 ? 8 : p == P32 ? 4 : 2; }
 inline int prec_vec(int p) { return 16 / prec_bytes(p); }
+
+// Slice pairs per site and the padded fifth-dimension extent.
+__host__ __device__ constexpr int ls_half(int Ls) { return (Ls + 1) >> 1; }
+__host__ __device__ constexpr int ls_padded(int Ls) { return 2 * ls_half(Ls); }
 
 // Bytes of one stored link (18 or 12 reals) rounded up to 16.
 __host__ __device__ constexpr int link_bytes(int real_bytes, bool c12) {

@@ -25,7 +25,8 @@ __global__ void __launch_bounds__(256) k_force(const Geom g, const char* psi, co
   using R = typename Store<P>::R;
   constexpr int LB = link_bytes(sizeof(T), C12);
   const int Ls = g.Ls;
-  const size_t site_bytes = (size_t)Ls * 24 * sizeof(T);
+  const int Lsh = ls_half(Ls);
+  const size_t site_bytes = (size_t)Lsh * 2 * 24 * sizeof(T);
   const size_t half_bytes = (size_t)g.N4h * site_bytes;
   const int lane = threadIdx.x % nsg;
   const long link = (long)blockIdx.x * (blockDim.x / nsg) + threadIdx.x / nsg;
@@ -49,9 +50,9 @@ __global__ void __launch_bounds__(256) k_force(const Geom g, const char* psi, co
     const char* chi_f = chi + (1 - p) * half_bytes + (size_t)j * site_bytes;
     for (int s = lane; s < Ls; s += nsg) {
       R v[24], ha[12], hb[12];
-      load_spinor<P>(psi_f, s, Ls, v);
+      load_slice<P>(psi_f, s, Lsh, v);
       project<-1>(mu, v, ha);
-      load_spinor<P>(chi_x, s, Ls, v);
+      load_slice<P>(chi_x, s, Lsh, v);
       project<-1>(mu, v, hb);
 #pragma unroll
       for (int h = 0; h < 2; ++h)
@@ -64,9 +65,9 @@ __global__ void __launch_bounds__(256) k_force(const Geom g, const char* psi, co
             b1[(a * 3 + b) * 2] += xr * yr + xi * yi;
             b1[(a * 3 + b) * 2 + 1] += xi * yr - xr * yi;
           }
-      load_spinor<P>(psi_x, s, Ls, v);
+      load_slice<P>(psi_x, s, Lsh, v);
       project<+1>(mu, v, ha);
-      load_spinor<P>(chi_f, s, Ls, v);
+      load_slice<P>(chi_f, s, Lsh, v);
       project<+1>(mu, v, hb);
 #pragma unroll
       for (int h = 0; h < 2; ++h)

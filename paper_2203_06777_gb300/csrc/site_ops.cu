@@ -2,10 +2,11 @@
 // FP64-accumulated reductions and CG vector updates. All are bandwidth-bound passes over the
 // device field layout described in dwf_common.cuh.
 //
-// Elementwise kernels walk a field in units of 8 reals: unit (site, g, s) is reals 8g..8g+7 of
-// slice s of a site block. Consecutive threads take consecutive s, so every precision's
-// 16-byte vectors are read and written contiguously, and fields of different precisions (whose
-// chunks hold 2, 4 or 8 reals) can be combined in one pass.
+// Elementwise kernels walk a field in units of 16 values: unit (site, g, q) is reals 8g..8g+7 of
+// both slices of pair q of a site block, in the order [real][slice]. Consecutive threads take
+// consecutive pairs, so every precision's 16-byte vectors are read and written contiguously, and
+// fields of different precisions (whose vectors hold 1, 2 or 4 reals of two slices) can be
+// combined in one pass. Pad slices (odd Ls) are zero and stay zero.
 #include "dhop_kernel.cuh"
 #include "site_ops.cuh"
 
@@ -15,46 +16,48 @@ template <int P>
 using RT = typename Store<P>::R;
 
 template <int P>
-__device__ __forceinline__ const char* site_ptr(const void* base, long site, int Ls) {
-  return static_cast<const char*>(base) + (size_t)site * Ls * 24 * sizeof(typename Store<P>::T);
+__device__ __forceinline__ const char* site_ptr(const void* base, long site, int Lsh) {
+  return static_cast<const char*>(base) + (size_t)site * Lsh * 2 * 24 * sizeof(typename Store<P>::T);
 }
 
+// The 16 values of unit (site, g, q): NV = 8 / RV vectors, chunks g*NV .. g*NV + NV - 1.
 template <int P, bool COHERENT>
-__device__ __forceinline__ void ld8(const void* base, long site, int g, int s, int Ls, RT<P>* o) {
+__device__ __forceinline__ void ld_unit(const void* base, long site, int g, int q, int Lsh, RT<P>* o) {
   constexpr int VEC = Store<P>::VEC;
-  constexpr int NV = 8 / VEC;
-  const char* sb = site_ptr<P>(base, site, Ls);
+  constexpr int NV = 16 / VEC;
+  const char* sb = site_ptr<P>(base, site, Lsh);
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    const char* q = sb + ((size_t)(g * NV + v) * Ls + s) * 16;
+    const char* p = sb + ((size_t)(g * NV + v) * Lsh + q) * 16;
     if (COHERENT)
-      ld16c<P>(q, o + v * VEC);
+      ld16c<P>(p, o + v * VEC);
     else
-      ld16<P>(q, o + v * VEC);
+      ld16<P>(p, o + v * VEC);
   }
 }
 
 template <int P>
-__device__ __forceinline__ void st8(void* base, long site, int g, int s, int Ls, const RT<P>* o) {
+__device__ __forceinline__ void st_unit(void* base, long site, int g, int q, int Lsh, const RT<P>* o) {
   constexpr int VEC = Store<P>::VEC;
-  constexpr int NV = 8 / VEC;
-  char* sb = const_cast<char*>(site_ptr<P>(base, site, Ls));
+  constexpr int NV = 16 / VEC;
+  char* sb = const_cast<char*>(site_ptr<P>(base, site, Lsh));
 #pragma unroll
-  for (int v = 0; v < NV; ++v) st16<P>(sb + ((size_t)(g * NV + v) * Ls + s) * 16, o + v * VEC);
+  for (int v = 0; v < NV; ++v) st16<P>(sb + ((size_t)(g * NV + v) * Lsh + q) * 16, o + v * VEC);
 }
 
 template <int P>
-__device__ __forceinline__ void st8d(void* base, long site, int g, int s, int Ls, const double* o) {
+__device__ __forceinline__ void st_unit_d(void* base, long site, int g, int q, int Lsh, const double* o) {
   constexpr int VEC = Store<P>::VEC;
-  constexpr int NV = 8 / VEC;
-  char* sb = const_cast<char*>(site_ptr<P>(base, site, Ls));
+  constexpr int NV = 16 / VEC;
+  char* sb = const_cast<char*>(site_ptr<P>(base, site, Lsh));
 #pragma unroll
-  for (int v = 0; v < NV; ++v) st16d<P>(sb + ((size_t)(g * NV + v) * Ls + s) * 16, o + v * VEC);
+  for (int v = 0; v < NV; ++v) st16d<P>(sb + ((size_t)(g * NV + v) * Lsh + q) * 16, o + v * VEC);
 }
 
-__device__ __forceinline__ void unit_coords(long u, int Ls, long& site, int& g, int& s) {
-  const long rem = u / Ls;
-  s = (int)(u - rem * Ls);
+// Value i of a unit is real 8g + (i >> 1) of slice 2q + (i & 1).
+__device__ __forceinline__ void unit_coords(long u, int Lsh, long& site, int& g, int& q) {
+  const long rem = u / Lsh;
+  q = (int)(u - rem * Lsh);
   site = rem / 3;
   g = (int)(rem - site * 3);
 }
@@ -131,13 +134,14 @@ static cudaError_t finalize(const double* partials, int ncomp, double* scal, int
 template <int P>
 __global__ void k_pack_spinor(Geom g, double* canon, char* field, int parity0, int nparity, bool unpack) {
   using R = RT<P>;
-  constexpr int VEC = Store<P>::VEC, NCH = 24 / VEC;
+  constexpr int VEC = Store<P>::VEC, RV = Store<P>::RV, NCH = Store<P>::NCH;
   const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
   const int Ls = g.Ls;
-  const long total = (long)nparity * g.N4h * NCH * Ls;
+  const int Lsh = ls_half(Ls);
+  const long total = (long)nparity * g.N4h * NCH * Lsh;
   if (tid >= total) return;
-  const long rem = tid / Ls;
-  const int s = (int)(tid - rem * Ls);
+  const long rem = tid / Lsh;
+  const int q = (int)(tid - rem * Lsh);
   const long sitep = rem / NCH;
   const int k = (int)(rem - sitep * NCH);
   const int ph = (int)(sitep / g.N4h);
@@ -145,18 +149,24 @@ __global__ void k_pack_spinor(Geom g, double* canon, char* field, int parity0, i
   int c[4];
   cb_coords(g, i, parity0 + ph, c);
   const long lex = c[0] + (long)g.L[0] * (c[1] + (long)g.L[1] * (c[2] + (long)g.L[2] * c[3]));
-  double* cp = canon + ((lex * Ls + s) * 24 + k * VEC);
-  char* fp = field + (size_t)sitep * Ls * 24 * sizeof(typename Store<P>::T) + ((size_t)k * Ls + s) * 16;
+  char* fp = field + (size_t)sitep * Lsh * 2 * 24 * sizeof(typename Store<P>::T) + ((size_t)k * Lsh + q) * 16;
+  // value 2j + l of the vector is real RV*k + j of slice 2q + l
   if (!unpack) {
     double v[VEC];
 #pragma unroll
-    for (int j = 0; j < VEC; ++j) v[j] = cp[j];
+    for (int e = 0; e < VEC; ++e) {
+      const int s = 2 * q + (e & 1);
+      v[e] = s < Ls ? canon[(lex * Ls + s) * 24 + RV * k + (e >> 1)] : 0.0;
+    }
     st16d<P>(fp, v);
   } else {
     R v[VEC];
     ld16<P>(fp, v);
 #pragma unroll
-    for (int j = 0; j < VEC; ++j) cp[j] = (double)v[j];
+    for (int e = 0; e < VEC; ++e) {
+      const int s = 2 * q + (e & 1);
+      if (s < Ls) canon[(lex * Ls + s) * 24 + RV * k + (e >> 1)] = (double)v[e];
+    }
   }
 }
 
@@ -164,7 +174,7 @@ cudaError_t launch_pack_spinor(int prec, const Geom& g, const double* canon, voi
                                cudaStream_t st) {
   const int parity0 = subset == 2 ? 0 : subset;
   const int nparity = subset == 2 ? 2 : 1;
-  const long total = (long)nparity * g.N4h * (24 / prec_vec(prec)) * g.Ls;
+  const long total = (long)nparity * g.N4h * (24 / (prec_vec(prec) / 2)) * ls_half(g.Ls);
   const int blocks = grid_for(total, 256);
   double* c = const_cast<double*>(canon);
   char* f = static_cast<char*>(field);
@@ -229,31 +239,32 @@ __global__ void k_convert(const void* src, void* dst, long nsites, int Ls, const
   using RS = RT<PS>;
   using RD = RT<PD>;
   const double sc = scale_dev ? *scale_dev : scale;
-  const long units = nsites * 3 * Ls;
+  const int Lsh = ls_half(Ls);
+  const long units = nsites * 3 * Lsh;
   for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < units; u += (long)gridDim.x * blockDim.x) {
     long site;
-    int g, s;
-    unit_coords(u, Ls, site, g, s);
-    RS a[8];
-    ld8<PS, false>(src, site, g, s, Ls, a);
+    int g, q;
+    unit_coords(u, Lsh, site, g, q);
+    RS a[16];
+    ld_unit<PS, false>(src, site, g, q, Lsh, a);
     if constexpr (PS == P64 || PD == P64) {
-      double b[8];
+      double b[16];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) b[j] = (double)a[j] * sc;
-      st8d<PD>(dst, site, g, s, Ls, b);
+      for (int j = 0; j < 16; ++j) b[j] = (double)a[j] * sc;
+      st_unit_d<PD>(dst, site, g, q, Lsh, b);
     } else {
-      RD b[8];
+      RD b[16];
       const float f = (float)sc;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) b[j] = (RD)((float)a[j] * f);
-      st8<PD>(dst, site, g, s, Ls, b);
+      for (int j = 0; j < 16; ++j) b[j] = (RD)((float)a[j] * f);
+      st_unit<PD>(dst, site, g, q, Lsh, b);
     }
   }
 }
 
 cudaError_t launch_convert(int psrc, int pdst, const void* src, void* dst, long nsites, int Ls, const double* scale_dev,
                            double scale, cudaStream_t st) {
-  const int blocks = grid_for(nsites * 3 * Ls, 256);
+  const int blocks = grid_for(nsites * 3 * ls_half(Ls), 256);
 #define CV(A, B) k_convert<A, B><<<blocks, 256, 0, st>>>(src, dst, nsites, Ls, scale_dev, scale)
 #define CVROW(A)            \
   switch (pdst) {           \
@@ -282,19 +293,23 @@ __global__ void __launch_bounds__(256) k_mooee(const void* in, void* out, long n
                                                bool inverse, double d5, double mass, double inv_d5, double inv_den) {
   using R = RT<P>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* sm = reinterpret_cast<R*>(smem_raw);
+  R* sm = reinterpret_cast<R*>(smem_raw);  // [site][s < Ls][24]
+  const int Lsh = ls_half(Ls);
   const long site0 = (long)blockIdx.x * spc;
   const int ns = (int)min((long)spc, nsites - site0);
-  const int units = ns * 3 * Ls;
+  const int units = ns * 3 * Lsh;
   for (int u = threadIdx.x; u < units; u += blockDim.x) {
-    const int rem = u / Ls;
-    const int s = u - rem * Ls;
+    const int rem = u / Lsh;
+    const int q = u - rem * Lsh;
     const int sl = rem / 3;
     const int g = rem - sl * 3;
-    R v[8];
-    ld8<P, true>(in, site0 + sl, g, s, Ls, v);
+    R v[16];
+    ld_unit<P, true>(in, site0 + sl, g, q, Lsh, v);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) sm[((size_t)sl * Ls + s) * 24 + 8 * g + j] = v[j];
+    for (int i = 0; i < 16; ++i) {
+      const int s = 2 * q + (i & 1);
+      if (s < Ls) sm[((size_t)sl * Ls + s) * 24 + 8 * g + (i >> 1)] = v[i];
+    }
   }
   __syncthreads();
   if (inverse) {
@@ -306,32 +321,43 @@ __global__ void __launch_bounds__(256) k_mooee(const void* in, void* out, long n
     }
     __syncthreads();
     for (int u = threadIdx.x; u < units; u += blockDim.x) {
-      const int rem = u / Ls;
-      const int s = u - rem * Ls;
+      const int rem = u / Lsh;
+      const int q = u - rem * Lsh;
       const int sl = rem / 3;
       const int g = rem - sl * 3;
-      st8<P>(out, site0 + sl, g, s, Ls, sm + ((size_t)sl * Ls + s) * 24 + 8 * g);
+      R o[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int s = 2 * q + (i & 1);
+        o[i] = s < Ls ? sm[((size_t)sl * Ls + s) * 24 + 8 * g + (i >> 1)] : R(0);
+      }
+      st_unit<P>(out, site0 + sl, g, q, Lsh, o);
     }
     return;
   }
   for (int u = threadIdx.x; u < units; u += blockDim.x) {
-    const int rem = u / Ls;
-    const int s = u - rem * Ls;
+    const int rem = u / Lsh;
+    const int q = u - rem * Lsh;
     const int sl = rem / 3;
     const int g = rem - sl * 3;
-    const int sm1 = s > 0 ? s - 1 : Ls - 1, sp1 = s < Ls - 1 ? s + 1 : 0;
-    const R cm = s > 0 ? R(-1) : R(mass), cp = s < Ls - 1 ? R(-1) : R(mass);
-    const int s_up = dag ? sp1 : sm1, s_lo = dag ? sm1 : sp1;
-    const R c_up = dag ? cp : cm, c_lo = dag ? cm : cp;
     const R* base = sm + (size_t)sl * Ls * 24;
-    R o[8];
+    R o[16];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int r = 8 * g + j;
+    for (int i = 0; i < 16; ++i) {
+      const int s = 2 * q + (i & 1);
+      const int r = 8 * g + (i >> 1);
+      if (s >= Ls) {
+        o[i] = R(0);
+        continue;
+      }
+      const int sm1 = s > 0 ? s - 1 : Ls - 1, sp1 = s < Ls - 1 ? s + 1 : 0;
+      const R cm = s > 0 ? R(-1) : R(mass), cp = s < Ls - 1 ? R(-1) : R(mass);
+      const int s_up = dag ? sp1 : sm1, s_lo = dag ? sm1 : sp1;
+      const R c_up = dag ? cp : cm, c_lo = dag ? cm : cp;
       const bool upper = r < 12;
-      o[j] = R(d5) * base[s * 24 + r] + (upper ? c_up * base[s_up * 24 + r] : c_lo * base[s_lo * 24 + r]);
+      o[i] = R(d5) * base[s * 24 + r] + (upper ? c_up * base[s_up * 24 + r] : c_lo * base[s_lo * 24 + r]);
     }
-    st8<P>(out, site0 + sl, g, s, Ls, o);
+    st_unit<P>(out, site0 + sl, g, q, Lsh, o);
   }
 }
 
@@ -364,28 +390,32 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(const void* a, const voi
                                                         double* partials) {
   using R = RT<P>;
   double acc[2] = {0.0, 0.0};
-  const long units = nsites * 3 * Ls;
+  const int Lsh = ls_half(Ls);
+  const long units = nsites * 3 * Lsh;
   for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < units; u += (long)gridDim.x * blockDim.x) {
     long site;
-    int g, s;
-    unit_coords(u, Ls, site, g, s);
-    R x[8];
-    ld8<P, false>(a, site, g, s, Ls, x);
+    int g, q;
+    unit_coords(u, Lsh, site, g, q);
+    R x[16];
+    ld_unit<P, false>(a, site, g, q, Lsh, x);
     if (INNER) {
-      R y[8];
-      ld8<P, false>(b, site, g, s, Ls, y);
+      R y[16];
+      ld_unit<P, false>(b, site, g, q, Lsh, y);
       R re = 0, im = 0;
 #pragma unroll
-      for (int j = 0; j < 8; j += 2) {
-        re += x[j] * y[j] + x[j + 1] * y[j + 1];
-        im += x[j] * y[j + 1] - x[j + 1] * y[j];
-      }
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+          const int ir = (2 * c) * 2 + l, ii = (2 * c + 1) * 2 + l;  // re and im of one complex number
+          re += x[ir] * y[ir] + x[ii] * y[ii];
+          im += x[ir] * y[ii] - x[ii] * y[ir];
+        }
       acc[0] += (double)re;
       acc[1] += (double)im;
     } else {
       R t = 0;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) t += x[j] * x[j];
+      for (int j = 0; j < 16; ++j) t += x[j] * x[j];
       acc[0] += (double)t;
     }
   }
@@ -426,26 +456,27 @@ __global__ void __launch_bounds__(RED_THREADS) k_cg_xr(void* x, void* r, const v
   using RP = RT<PP>;
   const RX alpha = (RX)scal[S_ALPHA];
   double acc = 0.0;
-  const long units = nsites * 3 * Ls;
+  const int Lsh = ls_half(Ls);
+  const long units = nsites * 3 * Lsh;
   for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < units; u += (long)gridDim.x * blockDim.x) {
     long site;
-    int g, s;
-    unit_coords(u, Ls, site, g, s);
-    RX xv[8], rv[8];
-    RP pv[8], av[8];
-    ld8<PX, true>(x, site, g, s, Ls, xv);
-    ld8<PX, true>(r, site, g, s, Ls, rv);
-    ld8<PP, false>(p, site, g, s, Ls, pv);
-    ld8<PP, false>(Ap, site, g, s, Ls, av);
+    int g, q;
+    unit_coords(u, Lsh, site, g, q);
+    RX xv[16], rv[16];
+    RP pv[16], av[16];
+    ld_unit<PX, true>(x, site, g, q, Lsh, xv);
+    ld_unit<PX, true>(r, site, g, q, Lsh, rv);
+    ld_unit<PP, false>(p, site, g, q, Lsh, pv);
+    ld_unit<PP, false>(Ap, site, g, q, Lsh, av);
     RX t = 0;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+    for (int j = 0; j < 16; ++j) {
       xv[j] += alpha * (RX)pv[j];
       rv[j] -= alpha * (RX)av[j];
       t += rv[j] * rv[j];
     }
-    st8<PX>(x, site, g, s, Ls, xv);
-    st8<PX>(r, site, g, s, Ls, rv);
+    st_unit<PX>(x, site, g, q, Lsh, xv);
+    st_unit<PX>(r, site, g, q, Lsh, rv);
     acc += (double)t;
   }
   double v[1] = {acc};
@@ -457,18 +488,19 @@ __global__ void k_cg_p(const void* r, void* p, long nsites, int Ls, const double
   using RX = RT<PX>;
   using RP = RT<PP>;
   const RX beta = (RX)scal[S_BETA];
-  const long units = nsites * 3 * Ls;
+  const int Lsh = ls_half(Ls);
+  const long units = nsites * 3 * Lsh;
   for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < units; u += (long)gridDim.x * blockDim.x) {
     long site;
-    int g, s;
-    unit_coords(u, Ls, site, g, s);
-    RX rv[8];
-    RP pv[8];
-    ld8<PX, false>(r, site, g, s, Ls, rv);
-    ld8<PP, true>(p, site, g, s, Ls, pv);
+    int g, q;
+    unit_coords(u, Lsh, site, g, q);
+    RX rv[16];
+    RP pv[16];
+    ld_unit<PX, false>(r, site, g, q, Lsh, rv);
+    ld_unit<PP, true>(p, site, g, q, Lsh, pv);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) pv[j] = (RP)(rv[j] + beta * (RX)pv[j]);
-    st8<PP>(p, site, g, s, Ls, pv);
+    for (int j = 0; j < 16; ++j) pv[j] = (RP)(rv[j] + beta * (RX)pv[j]);
+    st_unit<PP>(p, site, g, q, Lsh, pv);
   }
 }
 
@@ -494,7 +526,7 @@ cudaError_t launch_cg_xr(int px, int pp, void* x, void* r, const void* p, const 
 
 cudaError_t launch_cg_p(int px, int pp, const void* r, void* p, long nsites, int Ls, const double* scal,
                         cudaStream_t st) {
-  const int blocks = grid_for(nsites * 3 * Ls, 256);
+  const int blocks = grid_for(nsites * 3 * ls_half(Ls), 256);
 #define PU(A, B)                                                              \
   if (px == A && pp == B) {                                                   \
     k_cg_p<A, B><<<blocks, 256, 0, st>>>(r, p, nsites, Ls, scal);             \
@@ -508,20 +540,21 @@ cudaError_t launch_cg_p(int px, int pp, const void* r, void* p, long nsites, int
 __global__ void __launch_bounds__(RED_THREADS) k_residual64(const void* b, const void* Ax, void* r, long nsites, int Ls,
                                                             double* partials) {
   double acc = 0.0;
-  const long units = nsites * 3 * Ls;
+  const int Lsh = ls_half(Ls);
+  const long units = nsites * 3 * Lsh;
   for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < units; u += (long)gridDim.x * blockDim.x) {
     long site;
-    int g, s;
-    unit_coords(u, Ls, site, g, s);
-    double bv[8], av[8];
-    ld8<P64, false>(b, site, g, s, Ls, bv);
-    ld8<P64, false>(Ax, site, g, s, Ls, av);
+    int g, q;
+    unit_coords(u, Lsh, site, g, q);
+    double bv[16], av[16];
+    ld_unit<P64, false>(b, site, g, q, Lsh, bv);
+    ld_unit<P64, false>(Ax, site, g, q, Lsh, av);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+    for (int j = 0; j < 16; ++j) {
       bv[j] -= av[j];
       acc += bv[j] * bv[j];
     }
-    st8<P64>(r, site, g, s, Ls, bv);
+    st_unit<P64>(r, site, g, q, Lsh, bv);
   }
   double v[1] = {acc};
   block_sum<1>(v, partials, RED_BLOCKS);
@@ -539,27 +572,28 @@ template <int PY>
 __global__ void k_accum_zero(void* x, void* y, long nsites, int Ls, const double* c_dev) {
   using RY = RT<PY>;
   const double c = *c_dev;
-  const long units = nsites * 3 * Ls;
+  const int Lsh = ls_half(Ls);
+  const long units = nsites * 3 * Lsh;
   for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < units; u += (long)gridDim.x * blockDim.x) {
     long site;
-    int g, s;
-    unit_coords(u, Ls, site, g, s);
-    double xv[8];
-    RY yv[8];
-    ld8<P64, true>(x, site, g, s, Ls, xv);
-    ld8<PY, true>(y, site, g, s, Ls, yv);
+    int g, q;
+    unit_coords(u, Lsh, site, g, q);
+    double xv[16];
+    RY yv[16];
+    ld_unit<P64, true>(x, site, g, q, Lsh, xv);
+    ld_unit<PY, true>(y, site, g, q, Lsh, yv);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+    for (int j = 0; j < 16; ++j) {
       xv[j] += c * (double)yv[j];
       yv[j] = RY(0);
     }
-    st8<P64>(x, site, g, s, Ls, xv);
-    st8<PY>(y, site, g, s, Ls, yv);
+    st_unit<P64>(x, site, g, q, Lsh, xv);
+    st_unit<PY>(y, site, g, q, Lsh, yv);
   }
 }
 
 cudaError_t launch_accum_zero(int py, void* x, void* y, long nsites, int Ls, const double* c_dev, cudaStream_t st) {
-  const int blocks = grid_for(nsites * 3 * Ls, 256);
+  const int blocks = grid_for(nsites * 3 * ls_half(Ls), 256);
   switch (py) {
     case P64: k_accum_zero<P64><<<blocks, 256, 0, st>>>(x, y, nsites, Ls, c_dev); break;
     case P32: k_accum_zero<P32><<<blocks, 256, 0, st>>>(x, y, nsites, Ls, c_dev); break;
@@ -571,22 +605,23 @@ cudaError_t launch_accum_zero(int py, void* x, void* y, long nsites, int Ls, con
 template <int P>
 __global__ void k_axpby(double a, const void* x, double b, void* y, long nsites, int Ls) {
   using R = RT<P>;
-  const long units = nsites * 3 * Ls;
+  const int Lsh = ls_half(Ls);
+  const long units = nsites * 3 * Lsh;
   for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < units; u += (long)gridDim.x * blockDim.x) {
     long site;
-    int g, s;
-    unit_coords(u, Ls, site, g, s);
-    R xv[8], yv[8];
-    ld8<P, true>(x, site, g, s, Ls, xv);
-    ld8<P, true>(y, site, g, s, Ls, yv);
+    int g, q;
+    unit_coords(u, Lsh, site, g, q);
+    R xv[16], yv[16];
+    ld_unit<P, true>(x, site, g, q, Lsh, xv);
+    ld_unit<P, true>(y, site, g, q, Lsh, yv);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) yv[j] = R(a) * xv[j] + R(b) * yv[j];
-    st8<P>(y, site, g, s, Ls, yv);
+    for (int j = 0; j < 16; ++j) yv[j] = R(a) * xv[j] + R(b) * yv[j];
+    st_unit<P>(y, site, g, q, Lsh, yv);
   }
 }
 
 cudaError_t launch_axpby(int p, double a, const void* x, double b, void* y, long nsites, int Ls, cudaStream_t st) {
-  const int blocks = grid_for(nsites * 3 * Ls, 256);
+  const int blocks = grid_for(nsites * 3 * ls_half(Ls), 256);
   switch (p) {
     case P64: k_axpby<P64><<<blocks, 256, 0, st>>>(a, x, b, y, nsites, Ls); break;
     case P32: k_axpby<P32><<<blocks, 256, 0, st>>>(a, x, b, y, nsites, Ls); break;
@@ -603,7 +638,7 @@ cudaError_t launch_axpby(int p, double a, const void* x, double b, void* y, long
 // grid_dwf_inner_noalloc: the same FP64-accumulated reduction as launch_reduce, for callers
 // that must not allocate device memory, with its scratch in a fixed array that is part of the
 // library's device image instead of a cudaMalloc'd buffer. Each CTA reduces one contiguous
-// chunk of NOALLOC_UNITS_PER_CTA units (8 reals each), so the number of partial sums, and with
+// chunk of NOALLOC_UNITS_PER_CTA units (16 values each), so the number of partial sums, and with
 // it the largest field accepted, is bounded by the array.
 
 namespace gdwf {
@@ -622,32 +657,36 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_chunked(const void* a, c
                                                                 double* partials, int nblocks) {
   using R = RT<P>;
   double acc[2] = {0.0, 0.0};
-  const long units = nsites * 3 * Ls;
+  const int Lsh = ls_half(Ls);
+  const long units = nsites * 3 * Lsh;
   const long first = (long)blockIdx.x * NOALLOC_UNITS_PER_CTA;
 #pragma unroll
   for (int k = 0; k < NOALLOC_UNITS_PER_THREAD; ++k) {
     const long u = first + threadIdx.x + (long)k * RED_THREADS;
     if (u >= units) break;
     long site;
-    int g, s;
-    unit_coords(u, Ls, site, g, s);
-    R x[8];
-    ld8<P, false>(a, site, g, s, Ls, x);
+    int g, q;
+    unit_coords(u, Lsh, site, g, q);
+    R x[16];
+    ld_unit<P, false>(a, site, g, q, Lsh, x);
     if (INNER) {
-      R y[8];
-      ld8<P, false>(b, site, g, s, Ls, y);
+      R y[16];
+      ld_unit<P, false>(b, site, g, q, Lsh, y);
       R re = 0, im = 0;
 #pragma unroll
-      for (int j = 0; j < 8; j += 2) {
-        re += x[j] * y[j] + x[j + 1] * y[j + 1];
-        im += x[j] * y[j + 1] - x[j + 1] * y[j];
-      }
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+          const int ir = (2 * c) * 2 + l, ii = (2 * c + 1) * 2 + l;  // re and im of one complex number
+          re += x[ir] * y[ir] + x[ii] * y[ii];
+          im += x[ir] * y[ii] - x[ii] * y[ir];
+        }
       acc[0] += (double)re;
       acc[1] += (double)im;
     } else {
       R t = 0;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) t += x[j] * x[j];
+      for (int j = 0; j < 16; ++j) t += x[j] * x[j];
       acc[0] += (double)t;
     }
   }
@@ -708,14 +747,15 @@ extern "C" int grid_dwf_inner_noalloc(int precision, const void* a, const void* 
   if (reinterpret_cast<uintptr_t>(a) % 16 || (b && reinterpret_cast<uintptr_t>(b) % 16) ||
       reinterpret_cast<uintptr_t>(result) % 8)
     return noalloc_error(err, err_len, GRID_DWF_ERR_INVALID_ARG, "grid_dwf_inner_noalloc: misaligned pointer");
-  const long units = nsites * 3L * Ls;
+  const long Lsh = ls_half(Ls);
+  const long units = nsites * 3L * Lsh;  // 16 values (8 reals of a slice pair) each
   const long nblocks = (units + NOALLOC_UNITS_PER_CTA - 1) / NOALLOC_UNITS_PER_CTA;
-  if (nsites > 0 && (units / 3 / Ls != nsites || nblocks > NOALLOC_MAX_PARTIALS))
+  if (nsites > 0 && (units / 3 / Lsh != nsites || nblocks > NOALLOC_MAX_PARTIALS))
     return noalloc_error(err, err_len, GRID_DWF_ERR_INVALID_ARG,
                          "grid_dwf_inner_noalloc: field of " + std::to_string(nsites) + " sites x Ls " +
                              std::to_string(Ls) + " exceeds the static scratch (at most " +
-                             std::to_string((long)NOALLOC_MAX_PARTIALS * NOALLOC_UNITS_PER_CTA / 3) +
-                             " five-dimensional sites, nsites * Ls)");
+                             std::to_string((long)NOALLOC_MAX_PARTIALS * NOALLOC_UNITS_PER_CTA / 3 * 2) +
+                             " five-dimensional sites, nsites * Ls rounded up to even)");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess)

@@ -6,7 +6,8 @@ There is no CPU fallback: :func:`load` raises if the library cannot be built or 
 :class:`GridDWF` raises if no CUDA device is present.
 
 Fields on the device are flat real tensors in the library's device layout (one checkerboard half
-holds V/2 * Ls * 24 reals, a full field twice that); their torch dtype selects the storage
+holds V/2 * Lsp * 24 reals with Lsp = Ls rounded up to even, a full field twice that); their
+torch dtype selects the storage
 precision: float64 -> FP64, float32 -> FP32, float16 -> FP16, bfloat16 -> BF16. Canonical
 fields are complex128 tensors ``psi[t, z, y, x, s, spin, colour]`` and ``U[t, z, y, x, mu, a, b]``.
 """
@@ -141,7 +142,9 @@ class GridDWF:
         self.bc = tuple(int(b) for b in bc)
         self.compress12 = bool(compress12)
         self.half_sites = int(np.prod(self.dims)) // 2
-        self.half_reals = self.half_sites * self.Ls * 24
+        # device layout: Ls padded to even (slice pairs), so a half field holds V/2 * Lsp * 24 reals
+        self.Ls_padded = self.Ls + (self.Ls & 1)
+        self.half_reals = self.half_sites * self.Ls_padded * 24
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             rc = self.lib.grid_dwf_create(_ints(self.dims), self.Ls, self.M5, self.mass, _ints(self.bc),

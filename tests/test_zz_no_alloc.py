@@ -16,7 +16,7 @@ from paper_2203_06777_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-MAX_SITES_X_LS = 11184810  # the documented limit: nsites * Ls five-dimensional sites
+MAX_SITES_X_LS = 22369620  # the documented limit: nsites * Ls (rounded up to even) five-dimensional sites
 TOL = {0: 1e-13, 1: 1e-6, 2: 1e-6, 3: 1e-6}
 
 
