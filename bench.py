@@ -235,32 +235,56 @@ def time_dhop(dwf, torch, sets, steps, warmup, world):
 
 
 def time_dhop_e2e(dwf, torch, sets, steps, warmup, world):
-    """The same Dhop through the public API with host buffers: pinned host -> device copy of the
-    input, the two half-lattice launches, device -> pinned host copy of the result, every step."""
+    """The same Dhop through the public API with host buffers, as a streaming user runs it: each
+    step copies its input from pinned host memory to the device, applies the two half-lattice
+    hops and copies the result back to pinned host memory. Copies run on their own streams and
+    two device buffer sets alternate, so step i's transfers overlap step i-1's and i+1's
+    compute; events order every buffer reuse. Timed from the first copy to the last result."""
     op, src, dst = sets[0]
     half = op.half_reals
-    host_in = torch.empty(src.shape, dtype=src.dtype, pin_memory=True)
-    host_in.copy_(src)
-    host_out = torch.empty(dst.shape, dtype=dst.dtype, pin_memory=True)
-    dev_in = torch.empty_like(src)
-    dev_out = torch.empty_like(dst)
-    stream = torch.cuda.current_stream()
+    nbuf = 2
+    host_in = [torch.empty(src.shape, dtype=src.dtype, pin_memory=True) for _ in range(nbuf)]
+    host_out = [torch.empty(dst.shape, dtype=dst.dtype, pin_memory=True) for _ in range(nbuf)]
+    for h in host_in:
+        h.copy_(src)
+    dev_in = [torch.empty_like(src) for _ in range(nbuf)]
+    dev_out = [torch.empty_like(dst) for _ in range(nbuf)]
+    s_h2d, s_cmp, s_d2h = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    ev_in = [torch.cuda.Event() for _ in range(nbuf)]     # input copied
+    ev_done = [torch.cuda.Event() for _ in range(nbuf)]   # compute finished
+    ev_out = [torch.cuda.Event() for _ in range(nbuf)]    # result copied back
+    for b in range(nbuf):
+        ev_out[b].record(s_d2h)
 
-    def step():
-        dev_in.copy_(host_in, non_blocking=True)
-        op.dhop(dev_in[half:], dwf.EVEN, out=dev_out[:half])
-        op.dhop(dev_in[:half], dwf.ODD, out=dev_out[half:])
-        host_out.copy_(dev_out, non_blocking=True)
+    def step(i):
+        b = i % nbuf
+        with torch.cuda.stream(s_h2d):
+            s_h2d.wait_event(ev_done[b])  # the compute that last read dev_in[b] is done
+            dev_in[b].copy_(host_in[b], non_blocking=True)
+            ev_in[b].record(s_h2d)
+        with torch.cuda.stream(s_cmp):
+            s_cmp.wait_event(ev_in[b])
+            s_cmp.wait_event(ev_out[b])  # dev_out[b] has been copied back
+            op.dhop(dev_in[b][half:], dwf.EVEN, out=dev_out[b][:half])
+            op.dhop(dev_in[b][:half], dwf.ODD, out=dev_out[b][half:])
+            ev_done[b].record(s_cmp)
+        with torch.cuda.stream(s_d2h):
+            s_d2h.wait_event(ev_done[b])
+            host_out[b].copy_(dev_out[b], non_blocking=True)
+            ev_out[b].record(s_d2h)
 
-    for _ in range(warmup):
-        step()
+    for i in range(warmup):
+        step(i)
     torch.cuda.synchronize()
     barrier(world)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
-        step()
-    e1.record(stream)
+    e0.record(s_h2d)
+    s_cmp.wait_event(e0)
+    s_d2h.wait_event(e0)
+    for i in range(steps):
+        step(warmup + i)
+    s_h2d.wait_stream(s_d2h)
+    e1.record(s_h2d)
     torch.cuda.synchronize()
     barrier(world)
     nbytes = src.numel() * src.element_size()
@@ -296,6 +320,37 @@ def run_cg(dwf, torch, spec, maxiter=20000):
     out["tol"] = 1e-10
     op.close()
     return out
+
+
+def run_force(dwf, torch, spec, reps=20):
+    """Action and force (FP32 fields, FP64 accumulation) on the 16^4 x 16 derivative-timing
+    workload: S = |M psi|^2, the su(3) force and the ambient gradient, per call."""
+    dims, Ls = spec["dims"], spec["Ls"]
+    U = synth.random_gauge(dims, seed=1000 * spec["case"], eps=spec["eps"])
+    op = dwf.GridDWF(dims, Ls, spec["M5"], spec["mass"], bc=BC)
+    op.set_gauge(torch.from_numpy(U).cuda())
+    f = op.pack(torch.from_numpy(synth.random_spinor(dims, Ls, seed=1000 * spec["case"] + 1)).cuda(), dwf.FP32,
+                dwf.FULL)
+    shape = (dims[3], dims[2], dims[1], dims[0], 4, 3, 3)
+    F = torch.empty(shape, dtype=torch.complex128, device="cuda")
+    G = torch.empty(shape, dtype=torch.complex128, device="cuda")
+    chi = op.field(dwf.FP32, dwf.FULL)
+    for _ in range(3):
+        op.force(f, chi=chi)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        op.lib.grid_dwf_set_stream(op._h, dwf._ptr(torch.cuda.current_stream().cuda_stream))
+        rc = op.lib.grid_dwf_force(op._h, dwf.FP32, dwf._ptr(f), dwf._ptr(chi), dwf._ptr(F), dwf._ptr(G), None)
+        assert rc == 0
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    op.close()
+    return {"workload": "dwf_16x16x16x16_ls16_haar", "ms_per_force": round(ms, 4), "reps": reps,
+            "precision": "fp32 fields, fp64 accumulation",
+            "includes": "M psi (2 fused Dhop+Mooee launches), |M psi|^2, force and ambient-gradient kernel"}
 
 
 def cpu_baseline_sample(spec, target_seconds=10.0):
@@ -413,6 +468,8 @@ def gpu_arm(args):
     }
     if not args.no_cg and rank == 0:
         line["cg"] = run_cg(dwf, torch, synth.WORKLOADS[CG_WORKLOAD])
+    if not args.no_force and rank == 0:
+        line["force"] = run_force(dwf, torch, synth.WORKLOADS["dwf_16x16x16x16_ls16_haar"])
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline_sample(spec)
     barrier(world)
@@ -470,6 +527,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cg", action="store_true", help="skip the CG time-to-solution comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-force", action="store_true", help="skip the action/force timing")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

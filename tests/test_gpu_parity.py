@@ -375,3 +375,83 @@ def test_staged_cg_fp16(dwf, oracle_lib, staged):
     assert st.converged and st.true_residual <= 1e-10
     r = b - oracle_lib.m(dims, Ls, M5, MASS, BC, U, host(op.unpack(x)))
     assert np.linalg.norm(r) / np.linalg.norm(b) < 1e-8
+
+
+# ---------------------------------------------------------------- full-size workloads
+# The benchmark's 16^4 x 16 lattice, compared over the whole field (the oracle takes a few
+# seconds on the host cores), and the 32^4 x 16 lattice on sampled sites: the oracle's per-site
+# hopping term at 256 random 4D sites (all slices) against the same sites of the GPU output.
+
+
+def _workload(name):
+    return synth.WORKLOADS[name]
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+def test_full_size_dhop_16x16x16x16_ls16(dwf, oracle_lib, prec):
+    w = _workload("dwf_16x16x16x16_ls16_exp0.3")
+    dims, Ls = w["dims"], w["Ls"]
+    U = synth.random_gauge(dims, seed=1000 * w["case"], eps=w["eps"])
+    psi = synth.random_spinor(dims, Ls, seed=1000 * w["case"] + 1)
+    op = dwf.GridDWF(dims, Ls, w["M5"], w["mass"], bc=BC)
+    op.set_gauge(dev(U))
+    f = op.pack(dev(psi), prec, dwf.FULL)
+    half = op.half_reals
+    out = op.field(prec, dwf.FULL)
+    # the benchmark's launch configuration: two half-lattice applications
+    op.dhop(f[half:], dwf.EVEN, out=out[:half])
+    op.dhop(f[:half], dwf.ODD, out=out[half:])
+    got = host(op.unpack(out))
+    ref = oracle_lib.dhop(dims, Ls, BC, round_spinor(U, prec), round_spinor(psi, prec))
+    assert rel(got, ref) < TOL[prec], rel(got, ref)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_full_size_dhop_32x32x32x32_ls16_sampled(dwf, oracle_lib, prec):
+    w = _workload("dwf_32x32x32x32_ls16_exp0.5")
+    dims, Ls = w["dims"], w["Ls"]
+    U = synth.random_gauge(dims, seed=1000 * w["case"], eps=w["eps"])
+    psi = synth.random_spinor(dims, Ls, seed=1000 * w["case"] + 1)
+    op = dwf.GridDWF(dims, Ls, w["M5"], w["mass"], bc=BC)
+    op.set_gauge(dev(U))
+    f = op.pack(dev(psi), prec, dwf.FULL)
+    got = host(op.unpack(op.dhop(f, dwf.FULL))).reshape(-1, Ls, 4, 3)
+    rng = np.random.default_rng(77)
+    sites = rng.choice(int(np.prod(dims)), size=256, replace=False)
+    lx, ly, lz, lt = dims
+    # include the lattice corners, where every hop wraps around
+    sites = np.concatenate([sites, [0, lx - 1, lx * ly * lz * lt - 1]])
+    ref = oracle_lib.dhop_sites(dims, Ls, BC, round_spinor(U, prec), round_spinor(psi, prec), sites)
+    assert rel(got[sites], ref) < TOL[prec]
+
+
+def test_force_8x8x8x8_ls8_fd_and_oracle(dwf, oracle_lib):
+    """The derivative workload's check case: 8^4 x Ls=8, Haar links, FP64. The GPU force and
+    ambient gradient match the oracle's explicit formula, and central differences of the GPU's
+    own action along single link components (exact up to rounding: S is quadratic there)."""
+    w = synth.WORKLOADS["dwf_8x8x8x8_ls8_haar"]
+    dims, Ls = w["dims"], w["Ls"]
+    U = synth.random_gauge(dims, seed=1000 * w["case"])
+    psi = synth.random_spinor(dims, Ls, seed=1000 * w["case"] + 1)
+    op = dwf.GridDWF(dims, Ls, w["M5"], w["mass"], bc=BC)
+    op.set_gauge(dev(U))
+    f = op.pack(dev(psi), 0, dwf.FULL)
+    S, F, G = op.force(f)
+    S_ref, F_ref, G_ref = oracle_lib.force(dims, Ls, w["M5"], w["mass"], BC, U, psi)
+    assert abs(S - S_ref) < 1e-12 * S_ref
+    assert rel(host(F), F_ref) < 1e-12 and rel(host(G), G_ref) < 1e-12
+    Gh = host(G)
+    rng = np.random.default_rng(5)
+    hstep = 0.1
+    for _ in range(4):
+        idx = tuple(int(rng.integers(0, n)) for n in U.shape)
+        for unit in (1.0, 1j):
+            vals = []
+            for sgn in (1, -1):
+                Up = U.copy()
+                Up[idx] += sgn * hstep * unit
+                op.set_gauge(dev(Up))
+                vals.append(op.norm2(op.m(f)))
+            fd = (vals[0] - vals[1]) / (2 * hstep)
+            an = (np.conj(Gh[idx]) * unit).real
+            assert abs(fd - an) < 1e-9 * abs(an) + 1e-12 * S / hstep, (fd, an)
