@@ -52,8 +52,8 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# FP64 arithmetic ceiling of this part, measured with a DFMA throughput loop (2 flops per DFMA,
-# 152 SMs, no tensor cores): see the design notes. Dhop issues about 860 FP64 instructions per
+# FP64 arithmetic ceiling of this part: a DFMA throughput loop over all 152 SMs (2 flops per
+# DFMA, no FP64 tensor path) measured 1.17 TFLOP/s on a GB300. Dhop issues about 860 FP64 instructions per
 # 1320 flops, so its own ceiling is about 0.9 TFLOP/s.
 FP64_ALU_TFLOPS = 1.17
 

@@ -10,17 +10,18 @@
 // Because (1 -+ gamma_mu)/2 is a rank-2 projector, each spin sum is the sum over the two spins
 // of the projected half spinors: sum_spin a (x) [(1 - gamma) b]^+ = sum_{h=0,1} (P a)_h (x) (P b)_h^*.
 //
-// Thread mapping: nsg lanes per link (x, mu) split the Ls slices; each lane accumulates its
-// slices in the storage precision's arithmetic, the lanes are then combined in FP64 with warp
-// shuffles, and lane 0 multiplies by the link, projects and writes F and G in the canonical
-// FP64 layout [t][z][y][x][mu][3][3].
+// Thread mapping: one thread per link (x, mu), looping over the slices. FP32 fields: each slice
+// pair is projected and multiplied in packed FP32x2 arithmetic and summed in FP32 over blocks of
+// at most 8 pairs, each block then added into FP64 accumulators (GB300's FP64 pipe is 1/64 of
+// FP32, so per-pair FP64 adds would dominate the kernel); FP64 fields use FP64 throughout. The link algebra (U B1, B2 U^+, the traceless anti-Hermitian projection) is FP64,
+// and F and G are written in the canonical FP64 layout [t][z][y][x][mu][3][3].
 #include "dhop_kernel.cuh"
 
 namespace gdwf {
 
 template <int P, bool C12>
-__global__ void __launch_bounds__(256) k_force(const Geom g, const char* psi, const char* chi, const char* Ue,
-                                               const char* Uo, double* F, double* G, int nsg) {
+__global__ void __launch_bounds__(128) k_force(const Geom g, const char* psi, const char* chi, const char* Ue,
+                                               const char* Uo, double* F, double* G) {
   using T = typename Store<P>::T;
   using R = typename Store<P>::R;
   constexpr int LB = link_bytes(sizeof(T), C12);
@@ -28,75 +29,88 @@ __global__ void __launch_bounds__(256) k_force(const Geom g, const char* psi, co
   const int Lsh = ls_half(Ls);
   const size_t site_bytes = (size_t)Lsh * 2 * 24 * sizeof(T);
   const size_t half_bytes = (size_t)g.N4h * site_bytes;
-  const int lane = threadIdx.x % nsg;
-  const long link = (long)blockIdx.x * (blockDim.x / nsg) + threadIdx.x / nsg;
-  const bool active = link < 8L * g.N4h;
+  const long link = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (link >= 8L * g.N4h) return;
   const int mu = (int)(link & 3);
   const long rest = link >> 2;
   const int p = rest >= g.N4h ? 1 : 0;
   const int i = (int)(rest - (long)p * g.N4h);
+  int c[4];
+  cb_coords(g, i, p, c);
+  int ph;
+  const int j = cb_neighbour(g, i, c, mu, true, ph);
+  const char* psi_x = psi + p * half_bytes + (size_t)i * site_bytes;
+  const char* chi_x = chi + p * half_bytes + (size_t)i * site_bytes;
+  const char* psi_f = psi + (1 - p) * half_bytes + (size_t)j * site_bytes;
+  const char* chi_f = chi + (1 - p) * half_bytes + (size_t)j * site_bytes;
 
-  R b1[18], b2[18];
-#pragma unroll
-  for (int k = 0; k < 18; ++k) b1[k] = b2[k] = 0;
-  int c[4] = {0, 0, 0, 0};
-  int ph = 1;
-  if (active) {
-    cb_coords(g, i, p, c);
-    const int j = cb_neighbour(g, i, c, mu, true, ph);
-    const char* psi_x = psi + p * half_bytes + (size_t)i * site_bytes;
-    const char* chi_x = chi + p * half_bytes + (size_t)i * site_bytes;
-    const char* psi_f = psi + (1 - p) * half_bytes + (size_t)j * site_bytes;
-    const char* chi_f = chi + (1 - p) * half_bytes + (size_t)j * site_bytes;
-    for (int s = lane; s < Ls; s += nsg) {
-      R v[24], ha[12], hb[12];
-      load_slice<P>(psi_f, s, Lsh, v);
-      project<-1>(mu, v, ha);
-      load_slice<P>(chi_x, s, Lsh, v);
-      project<-1>(mu, v, hb);
-#pragma unroll
-      for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-          for (int b = 0; b < 3; ++b) {  // b1[a][b] += ha[h][a] conj(hb[h][b])
-            const R xr = ha[(h * 3 + a) * 2], xi = ha[(h * 3 + a) * 2 + 1];
-            const R yr = hb[(h * 3 + b) * 2], yi = hb[(h * 3 + b) * 2 + 1];
-            b1[(a * 3 + b) * 2] += xr * yr + xi * yi;
-            b1[(a * 3 + b) * 2 + 1] += xi * yr - xr * yi;
-          }
-      load_slice<P>(psi_x, s, Lsh, v);
-      project<+1>(mu, v, ha);
-      load_slice<P>(chi_f, s, Lsh, v);
-      project<+1>(mu, v, hb);
-#pragma unroll
-      for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-          for (int b = 0; b < 3; ++b) {
-            const R xr = ha[(h * 3 + a) * 2], xi = ha[(h * 3 + a) * 2 + 1];
-            const R yr = hb[(h * 3 + b) * 2], yi = hb[(h * 3 + b) * 2 + 1];
-            b2[(a * 3 + b) * 2] += xr * yr + xi * yi;
-            b2[(a * 3 + b) * 2 + 1] += xi * yr - xr * yi;
-          }
-    }
-  }
-  // combine the nsg lanes of this link in FP64
   double B1[18], B2[18];
 #pragma unroll
-  for (int k = 0; k < 18; ++k) {
-    B1[k] = (double)b1[k];
-    B2[k] = (double)b2[k];
-  }
-  for (int off = nsg / 2; off > 0; off >>= 1) {
+  for (int k = 0; k < 18; ++k) B1[k] = B2[k] = 0.0;
+  if constexpr (P == P64) {
 #pragma unroll
-    for (int k = 0; k < 18; ++k) {
-      B1[k] += __shfl_xor_sync(0xffffffffu, B1[k], off, nsg);
-      B2[k] += __shfl_xor_sync(0xffffffffu, B2[k], off, nsg);
+    for (int term = 0; term < 2; ++term) {
+      double* B = term == 0 ? B1 : B2;
+      const char* fa = term == 0 ? psi_f : psi_x;
+      const char* fb = term == 0 ? chi_x : chi_f;
+      for (int s = 0; s < Ls; ++s) {
+        double v[24], ha[12], hb[12];
+        load_lane64<0>(fa, s, Lsh, v);
+        if (term == 0) project<-1>(mu, v, ha); else project<+1>(mu, v, ha);
+        load_lane64<0>(fb, s, Lsh, v);
+        if (term == 0) project<-1>(mu, v, hb); else project<+1>(mu, v, hb);
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {  // B[a][b] += ha[h][a] conj(hb[h][b])
+              const double xr = ha[(h * 3 + a) * 2], xi = ha[(h * 3 + a) * 2 + 1];
+              const double yr = hb[(h * 3 + b) * 2], yi = hb[(h * 3 + b) * 2 + 1];
+              B[(a * 3 + b) * 2] = fma(xr, yr, fma(xi, yi, B[(a * 3 + b) * 2]));
+              B[(a * 3 + b) * 2 + 1] = fma(xi, yr, fma(-xr, yi, B[(a * 3 + b) * 2 + 1]));
+            }
+      }
+    }
+  } else {
+    // Pad slices are zero in every field, so pairs are used whole. Each term is summed in
+    // FP32x2 (one lane per slice parity) over blocks of up to FLUSH pairs, and each block's two
+    // lanes are added into the FP64 accumulators: at most 2 FLUSH FP32 terms per rounding chain.
+    constexpr int FLUSH = 8;
+#pragma unroll
+    for (int term = 0; term < 2; ++term) {
+      double* B = term == 0 ? B1 : B2;
+      const char* fa = term == 0 ? psi_f : psi_x;
+      const char* fb = term == 0 ? chi_x : chi_f;
+      for (int q0 = 0; q0 < Lsh; q0 += FLUSH) {
+        float2 acc[18];
+#pragma unroll
+        for (int k = 0; k < 18; ++k) acc[k] = make_float2(0.f, 0.f);
+        const int q1 = min(q0 + FLUSH, Lsh);
+        for (int q = q0; q < q1; ++q) {
+          float2 v[24], ha[12], hb[12];
+          load_pair<P, 0>(fa, q, Lsh, v);
+          if (term == 0) project2<-1>(mu, v, ha); else project2<+1>(mu, v, ha);
+          load_pair<P, 0>(fb, q, Lsh, v);
+          if (term == 0) project2<-1>(mu, v, hb); else project2<+1>(mu, v, hb);
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+              for (int b = 0; b < 3; ++b) {  // acc[a][b] += ha[h][a] conj(hb[h][b])
+                const float2 xr = ha[(h * 3 + a) * 2], xi = ha[(h * 3 + a) * 2 + 1];
+                const float2 yr = hb[(h * 3 + b) * 2], yi = hb[(h * 3 + b) * 2 + 1];
+                acc[(a * 3 + b) * 2] = ffma2(xr, yr, ffma2(xi, yi, acc[(a * 3 + b) * 2]));
+                acc[(a * 3 + b) * 2 + 1] =
+                    ffma2(xi, yr, ffma2(make_float2(-xr.x, -xr.y), yi, acc[(a * 3 + b) * 2 + 1]));
+              }
+        }
+#pragma unroll
+        for (int k = 0; k < 18; ++k) B[k] += (double)acc[k].x + (double)acc[k].y;
+      }
     }
   }
-  if (!active || lane != 0) return;
 
   R ur[18];
   load_link<P, C12>((p ? Uo : Ue) + ((size_t)i * 4 + mu) * LB, ur);
@@ -154,21 +168,18 @@ __global__ void __launch_bounds__(256) k_force(const Geom g, const char* psi, co
 
 cudaError_t launch_force(int prec, bool c12, const Geom& g, const void* psi, const void* chi, const void* Ue,
                          const void* Uo, double* F, double* G, cudaStream_t st) {
-  int nsg = 1;
-  while (nsg * 2 <= g.Ls && nsg < 8) nsg *= 2;
-  const int threads = 256;
+  const int threads = 128;
   const long links = 8L * g.N4h;
-  const int links_per_cta = threads / nsg;
-  const int blocks = (int)((links + links_per_cta - 1) / links_per_cta);
+  const int blocks = (int)((links + threads - 1) / threads);
   const char* ps = static_cast<const char*>(psi);
   const char* ch = static_cast<const char*>(chi);
   const char* e = static_cast<const char*>(Ue);
   const char* o = static_cast<const char*>(Uo);
-#define FK(P_)                                                                         \
-  if (c12)                                                                             \
-    k_force<P_, true><<<blocks, threads, 0, st>>>(g, ps, ch, e, o, F, G, nsg);         \
-  else                                                                                 \
-    k_force<P_, false><<<blocks, threads, 0, st>>>(g, ps, ch, e, o, F, G, nsg);
+#define FK(P_)                                                                   \
+  if (c12)                                                                       \
+    k_force<P_, true><<<blocks, threads, 0, st>>>(g, ps, ch, e, o, F, G);        \
+  else                                                                           \
+    k_force<P_, false><<<blocks, threads, 0, st>>>(g, ps, ch, e, o, F, G);
   switch (prec) {
     case P64: FK(P64) break;
     case P32: FK(P32) break;
