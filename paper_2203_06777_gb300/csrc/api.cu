@@ -9,7 +9,7 @@
 #include <string>
 
 #include "../../include/grid_dwf.h"
-#include "dhop_tma.cuh"
+#include "dhop_pipe.cuh"
 #include "site_ops.cuh"
 
 namespace gdwf {
@@ -37,6 +37,7 @@ struct grid_dwf {
   std::string err;
   bool sync_debug = false;
   bool staged = false;  // use the bulk-copy staged Dhop kernel where it applies (GRID_DWF_STAGED=1)
+  bool pipe = false;    // use the pipelined persistent Dhop kernel where it applies (GRID_DWF_PIPE=1)
 };
 
 namespace {
@@ -180,6 +181,19 @@ int dhop_half(grid_dwf_t* h, int prec, const void* in, void* out, int out_parity
     const size_t post_site = post != POST_NONE ? (size_t)h->Ls * 24 * rbytes : 0;
     a.seg = tma_choose_seg(h->g.Lxh, h->Ls, prec_bytes(prec), h->c12, post_site);
   }
+  a.pipe_rows = 0;
+  a.pipe_slots = 0;
+  if (h->pipe && a.seg == 0 && prec != GRID_DWF_FP64 && dhop_ls_specialised(h->Ls)) {
+    const int lb = link_bytes(prec_bytes(prec), h->c12);
+    int slots = 0;
+    const int R = pipe_choose_rows(h->g, prec_bytes(prec), lb, pre != PRE_NONE, post != POST_NONE, 200 * 1024, slots);
+    if (R > 0) {
+      a.pipe_rows = R;
+      a.pipe_slots = slots;
+      threads = R * h->g.Lxh * ls_half(h->Ls);
+      smem = pipe_plan(h->g, R, slots, prec_bytes(prec), lb, pre != PRE_NONE, post != POST_NONE).bytes;
+    }
+  }
   if (a.seg > 0) {
     threads = a.seg * ls_half(h->Ls);
     blocks = h->g.N4h / a.seg;
@@ -302,6 +316,8 @@ int grid_dwf_create(const int dims[4], int Ls, double M5, double mass, const int
   h->sync_debug = sd && sd[0] == '1';
   const char* sg = std::getenv("GRID_DWF_STAGED");
   h->staged = sg && sg[0] == '1';
+  const char* pp = std::getenv("GRID_DWF_PIPE");
+  h->pipe = pp && pp[0] == '1';
   cudaGetDevice(&h->device);
   cudaError_t e = cudaMalloc(&h->partials, sizeof(double) * 2 * RED_BLOCKS);
   if (e == cudaSuccess) e = cudaMalloc(&h->scal, sizeof(double) * S_COUNT);

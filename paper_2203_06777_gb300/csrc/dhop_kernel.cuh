@@ -52,6 +52,8 @@ struct DhopArgs {
   double inv_d5;   // 1 / (5 - M5)
   double inv_den;  // 1 / ((5 - M5) + m (5 - M5)^-(Ls-1))
   int seg;         // > 0: bulk-copy staged kernel with this many sites per CTA (dhop_tma.cuh)
+  int pipe_rows;   // > 0: pipelined persistent kernel with tiles of this many x-rows (dhop_pipe.cuh)
+  int pipe_slots;  //      and this many ring slots
   int* status;     // device status word: bit 0 set if a staged kernel's wait timed out
 };
 
@@ -422,10 +424,10 @@ __device__ __forceinline__ void store_lane64(char* blk, int s, int Lsh_rt, const
 }
 
 // Any precision: the 24 reals of slice s (the lane of its pair), in the arithmetic type.
-template <int P>
+template <int P, bool GLOBAL = true>
 __device__ __forceinline__ void load_slice(const char* blk, int s, int Lsh, typename Store<P>::R* v) {
   if constexpr (P == P64) {
-    load_lane64<0>(blk, s, Lsh, v);
+    load_lane64<0, GLOBAL>(blk, s, Lsh, v);
   } else {
     constexpr int VEC = Store<P>::VEC, RV = Store<P>::RV, NCH = Store<P>::NCH;
     const int l = s & 1;
@@ -433,7 +435,10 @@ __device__ __forceinline__ void load_slice(const char* blk, int s, int Lsh, type
 #pragma unroll
     for (int k = 0; k < NCH; ++k) {
       float t[VEC];
-      ld16<P>(b + (size_t)k * Lsh * 16, t);
+      if (GLOBAL)
+        ld16<P>(b + (size_t)k * Lsh * 16, t);
+      else
+        ld16c<P>(b + (size_t)k * Lsh * 16, t);
 #pragma unroll
       for (int j = 0; j < RV; ++j) v[RV * k + j] = t[2 * j + l];
     }
@@ -442,8 +447,8 @@ __device__ __forceinline__ void load_slice(const char* blk, int s, int Lsh, type
 
 // (Mooee aux)_s or (Mooee^+ aux)_s for one slice s < Ls (zero for the pad slice): the upper (P+)
 // reals couple to s-1 and the lower (P-) reals to s+1, with +m replacing -1 on the wrap-around;
-// the adjoint swaps them.
-template <int P, bool DAG5>
+// the adjoint swaps them. GLOBAL = false reads a block staged in shared memory.
+template <int P, bool DAG5, bool GLOBAL = true>
 __device__ __forceinline__ void mooee_slice(const char* blk, int s, int Ls, int Lsh, double d5, double mass,
                                             typename Store<P>::R* o) {
   using R = typename Store<P>::R;
@@ -460,9 +465,9 @@ __device__ __forceinline__ void mooee_slice(const char* blk, int s, int Ls, int 
   const R c_up = DAG5 ? cp : cm, c_lo = DAG5 ? cm : cp;
   const R d = R(d5);
   R self[24], up[24], lo[24];
-  load_slice<P>(blk, s, Lsh, self);
-  load_slice<P>(blk, s_up, Lsh, up);
-  load_slice<P>(blk, s_lo, Lsh, lo);
+  load_slice<P, GLOBAL>(blk, s, Lsh, self);
+  load_slice<P, GLOBAL>(blk, s_up, Lsh, up);
+  load_slice<P, GLOBAL>(blk, s_lo, Lsh, lo);
 #pragma unroll
   for (int r = 0; r < 24; ++r) o[r] = d * self[r] + (r < 12 ? c_up * up[r] : c_lo * lo[r]);
 }
