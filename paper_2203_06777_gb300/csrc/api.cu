@@ -9,7 +9,7 @@
 #include <string>
 
 #include "../../include/grid_dwf.h"
-#include "dhop_pipe.cuh"
+#include "dhop_tma.cuh"
 #include "site_ops.cuh"
 
 namespace gdwf {
@@ -37,7 +37,6 @@ struct grid_dwf {
   std::string err;
   bool sync_debug = false;
   bool staged = false;  // use the bulk-copy staged Dhop kernel where it applies (GRID_DWF_STAGED=1)
-  bool pipe = false;    // use the pipelined persistent Dhop kernel where it applies (GRID_DWF_PIPE=1)
 };
 
 namespace {
@@ -172,27 +171,13 @@ int dhop_half(grid_dwf_t* h, int prec, const void* in, void* out, int out_parity
   int threads = a.nsg * a.sites_per_cta;
   int blocks = (h->g.N4h + a.sites_per_cta - 1) / a.sites_per_cta;
   const size_t rbytes = prec == GRID_DWF_FP64 ? 8 : 4;
-  size_t smem = (dhop_stage_links(prec) ? dhop_link_smem_bytes(a.sites_per_cta, link_bytes(prec_bytes(prec), h->c12))
-                                        : 0) +
+  size_t smem = dhop_link_smem_bytes(prec, a.sites_per_cta, h->c12) +
                 (post != POST_NONE ? (size_t)a.sites_per_cta * h->Ls * 24 * rbytes : 0);
   // Staged (bulk-copy) kernel for the bandwidth-bound precisions when a row segment fits.
   a.seg = 0;
   if (h->staged && prec != GRID_DWF_FP64 && dhop_ls_specialised(h->Ls)) {
     const size_t post_site = post != POST_NONE ? (size_t)h->Ls * 24 * rbytes : 0;
     a.seg = tma_choose_seg(h->g.Lxh, h->Ls, prec_bytes(prec), h->c12, post_site);
-  }
-  a.pipe_rows = 0;
-  a.pipe_slots = 0;
-  if (h->pipe && a.seg == 0 && prec != GRID_DWF_FP64 && dhop_ls_specialised(h->Ls)) {
-    const int lb = link_bytes(prec_bytes(prec), h->c12);
-    int slots = 0;
-    const int R = pipe_choose_rows(h->g, prec_bytes(prec), lb, pre != PRE_NONE, post != POST_NONE, 200 * 1024, slots);
-    if (R > 0) {
-      a.pipe_rows = R;
-      a.pipe_slots = slots;
-      threads = R * h->g.Lxh * ls_half(h->Ls);
-      smem = pipe_plan(h->g, R, slots, prec_bytes(prec), lb, pre != PRE_NONE, post != POST_NONE).bytes;
-    }
   }
   if (a.seg > 0) {
     threads = a.seg * ls_half(h->Ls);
@@ -316,8 +301,6 @@ int grid_dwf_create(const int dims[4], int Ls, double M5, double mass, const int
   h->sync_debug = sd && sd[0] == '1';
   const char* sg = std::getenv("GRID_DWF_STAGED");
   h->staged = sg && sg[0] == '1';
-  const char* pp = std::getenv("GRID_DWF_PIPE");
-  h->pipe = pp && pp[0] == '1';
   cudaGetDevice(&h->device);
   cudaError_t e = cudaMalloc(&h->partials, sizeof(double) * 2 * RED_BLOCKS);
   if (e == cudaSuccess) e = cudaMalloc(&h->scal, sizeof(double) * S_COUNT);

@@ -52,8 +52,6 @@ struct DhopArgs {
   double inv_d5;   // 1 / (5 - M5)
   double inv_den;  // 1 / ((5 - M5) + m (5 - M5)^-(Ls-1))
   int seg;         // > 0: bulk-copy staged kernel with this many sites per CTA (dhop_tma.cuh)
-  int pipe_rows;   // > 0: pipelined persistent kernel with tiles of this many x-rows (dhop_pipe.cuh)
-  int pipe_slots;  //      and this many ring slots
   int* status;     // device status word: bit 0 set if a staged kernel's wait timed out
 };
 
@@ -238,14 +236,47 @@ __device__ __forceinline__ void copy_link(char* dst, const char* src) {
     *reinterpret_cast<uint4*>(dst + v * 16) = __ldg(reinterpret_cast<const uint4*>(src + v * 16));
 }
 
-// Whether the direct kernel stages each site's eight links in shared memory (FP32, FP64: the
-// broadcast link loads of all slice pairs cost more than the staging), or reads them directly
-// (FP16/BF16: 48-byte links, measured faster without staging).
-__host__ __device__ constexpr bool dhop_stage_links(int prec) { return prec == P32 || prec == P64; }
+// The direct kernel stages each site's eight links in shared memory once per CTA; every slice
+// pair of the site then reads them from there. FP64 keeps the stored format (18 or 12 doubles per
+// link). The packed kernels keep every link as 18 FP32 reals (80 bytes, converted from 16-bit
+// storage and with the third row rebuilt once per site instead of once per thread), and pad each
+// site's 640 bytes by 16: the four sites that one warp reads from then start 16 bytes apart
+// modulo 128 and their 16-byte reads fall in different banks instead of four-way conflicts.
+constexpr int DHOP_LINK_F32_BYTES = 80;
+__host__ __device__ constexpr int dhop_link_site_bytes(int prec, bool c12) {
+  return prec == P64 ? 8 * link_bytes(8, c12) : 8 * DHOP_LINK_F32_BYTES + 16;
+}
 
-// Shared memory of the staged links of one CTA (8 links per site), a multiple of 16 bytes.
-__host__ __device__ constexpr size_t dhop_link_smem_bytes(int sites_per_cta, int link_b) {
-  return (size_t)sites_per_cta * 8 * link_b;
+// Shared memory of the staged links of one CTA, a multiple of 16 bytes.
+__host__ __device__ constexpr size_t dhop_link_smem_bytes(int prec, int sites_per_cta, bool c12) {
+  return (size_t)sites_per_cta * dhop_link_site_bytes(prec, c12);
+}
+
+// One link from global memory (any storage precision, 18 or 12 reals) to shared memory as 18
+// FP32 reals.
+template <int P, bool C12>
+__device__ __forceinline__ void stage_link_f32(char* dst, const char* src) {
+  float u[18];
+  load_link<P, C12>(src, u);
+  float4* d = reinterpret_cast<float4*>(dst);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) d[v] = make_float4(u[4 * v], u[4 * v + 1], u[4 * v + 2], u[4 * v + 3]);
+  reinterpret_cast<float2*>(dst)[8] = make_float2(u[16], u[17]);
+}
+
+__device__ __forceinline__ void load_link_f32(const char* s, float* u) {
+  const float4* p = reinterpret_cast<const float4*>(s);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const float4 t = p[v];
+    u[4 * v] = t.x;
+    u[4 * v + 1] = t.y;
+    u[4 * v + 2] = t.z;
+    u[4 * v + 3] = t.w;
+  }
+  const float2 t = reinterpret_cast<const float2*>(s)[8];
+  u[16] = t.x;
+  u[17] = t.y;
 }
 
 // ---------------------------------------------------------------- packed two-slice algebra
@@ -363,6 +394,92 @@ __device__ __forceinline__ void accumulate2(int mu, const float2* uh, float c, f
   }
 }
 
+// ---------------------------------------------------------------- 16-bit storage projection
+// With FP16/BF16 storage every element of the half spinor is a + s b (s = +-1) of two stored
+// 16-bit values. Instead of widening both to FP32 and combining them with an FP32 FMA, the
+// FP32 <- 16-bit mixed-precision instructions of sm_100 and later take b as it is stored:
+// a is widened exactly (an FP32 add of -0, or for BF16 a shift into the upper half-word) and
+// a + s b is then one FP32 operation with one rounding (s b is exact), so the result is
+// bit-identical to widening both operands and computing in FP32, with half the conversions.
+// Conversions run on a narrower pipe than FMAs on this part and were what bounded the 16-bit
+// kernels.
+
+template <int P>
+__device__ __forceinline__ float widen16(unsigned short a) {
+  if constexpr (P == P16) {
+    float d;
+    asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(a), "f"(-0.0f));
+    return d;
+  } else {
+    return __uint_as_float((uint32_t)a << 16);
+  }
+}
+
+// a + S b in FP32 with one rounding; a already FP32, b a stored 16-bit value.
+template <int P, int S>
+__device__ __forceinline__ float add16(float a, unsigned short b) {
+  float d;
+  if constexpr (P == P16) {
+    if constexpr (S > 0)
+      asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(b), "f"(a));
+    else
+      asm("fma.rn.f32.f16 %0, %1, %2, %3;" : "=f"(d) : "h"(b), "h"((unsigned short)0xBC00), "f"(a));  // -1.0
+  } else {
+    if constexpr (S > 0)
+      asm("add.rn.f32.bf16 %0, %1, %2;" : "=f"(d) : "h"(b), "f"(a));
+    else
+      asm("fma.rn.f32.bf16 %0, %1, %2, %3;" : "=f"(d) : "h"(b), "h"((unsigned short)0xBF80), "f"(a));  // -1.0
+  }
+  return d;
+}
+
+// Both slices: word wa holds real a of slices (2q, 2q+1) as (low, high) 16-bit halves, wb real b.
+template <int P, int S>
+__device__ __forceinline__ float2 combine16(uint32_t wa, uint32_t wb) {
+  unsigned short alo, ahi, blo, bhi;
+  asm("mov.b32 {%0, %1}, %2;" : "=h"(alo), "=h"(ahi) : "r"(wa));
+  asm("mov.b32 {%0, %1}, %2;" : "=h"(blo), "=h"(bhi) : "r"(wb));
+  return make_float2(add16<P, S>(widen16<P>(alo), blo), add16<P, S>(widen16<P>(ahi), bhi));
+}
+
+// project2 on stored 16-bit words: w[r] holds real r of both slices of the pair.
+template <int P, int SIG>
+__device__ __forceinline__ void project2w(int mu, const uint32_t* w, float2* h) {
+#define WR(sp, c) w[((sp)*3 + (c)) * 2]
+#define WI(sp, c) w[((sp)*3 + (c)) * 2 + 1]
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float2 h0r, h0i, h1r, h1i;
+    if (mu == 0) {  // h0 = psi0 - SIG i psi3, h1 = psi1 - SIG i psi2
+      h0r = combine16<P, SIG>(WR(0, c), WI(3, c));
+      h0i = combine16<P, -SIG>(WI(0, c), WR(3, c));
+      h1r = combine16<P, SIG>(WR(1, c), WI(2, c));
+      h1i = combine16<P, -SIG>(WI(1, c), WR(2, c));
+    } else if (mu == 1) {  // h0 = psi0 - SIG psi3, h1 = psi1 + SIG psi2
+      h0r = combine16<P, -SIG>(WR(0, c), WR(3, c));
+      h0i = combine16<P, -SIG>(WI(0, c), WI(3, c));
+      h1r = combine16<P, SIG>(WR(1, c), WR(2, c));
+      h1i = combine16<P, SIG>(WI(1, c), WI(2, c));
+    } else if (mu == 2) {  // h0 = psi0 - SIG i psi2, h1 = psi1 + SIG i psi3
+      h0r = combine16<P, SIG>(WR(0, c), WI(2, c));
+      h0i = combine16<P, -SIG>(WI(0, c), WR(2, c));
+      h1r = combine16<P, -SIG>(WR(1, c), WI(3, c));
+      h1i = combine16<P, SIG>(WI(1, c), WR(3, c));
+    } else {  // h0 = psi0 + SIG psi2, h1 = psi1 + SIG psi3
+      h0r = combine16<P, SIG>(WR(0, c), WR(2, c));
+      h0i = combine16<P, SIG>(WI(0, c), WI(2, c));
+      h1r = combine16<P, SIG>(WR(1, c), WR(3, c));
+      h1i = combine16<P, SIG>(WI(1, c), WI(3, c));
+    }
+    h[(0 * 3 + c) * 2] = h0r;
+    h[(0 * 3 + c) * 2 + 1] = h0i;
+    h[(1 * 3 + c) * 2] = h1r;
+    h[(1 * 3 + c) * 2 + 1] = h1i;
+  }
+#undef WR
+#undef WI
+}
+
 // ---------------------------------------------------------------- layout accessors
 // Site blocks are [chunk k][pair q] of 16-byte vectors (dwf_common.cuh). LSH > 0 fixes the
 // number of pairs at compile time, so chunk offsets become immediates.
@@ -383,6 +500,22 @@ __device__ __forceinline__ void load_pair(const char* blk, int q, int Lsh_rt, fl
       ld16c<P>(b + (size_t)k * Lsh * 16, t);
 #pragma unroll
     for (int j = 0; j < RV; ++j) v[RV * k + j] = make_float2(t[2 * j], t[2 * j + 1]);
+  }
+}
+
+// 16-bit storage: the 24 stored words of pair q (word r = real r of both slices), not widened.
+template <int P, int LSH>
+__device__ __forceinline__ void load_words(const char* blk, int q, int Lsh_rt, uint32_t* w) {
+  static_assert(P == P16 || P == PB16, "16-bit storage only");
+  const int Lsh = LSH > 0 ? LSH : Lsh_rt;
+  const char* b = blk + (size_t)q * 16;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(b + (size_t)k * Lsh * 16));
+    w[4 * k] = v.x;
+    w[4 * k + 1] = v.y;
+    w[4 * k + 2] = v.z;
+    w[4 * k + 3] = v.w;
   }
 }
 
@@ -501,8 +634,9 @@ __device__ __forceinline__ void mooee_inv_line(R* v, int Ls, bool forward_form, 
 
 // ---------------------------------------------------------------- kernel bodies
 
-// FP32 / FP16 / BF16: one thread per (site, slice pair), packed two-wide arithmetic.
-template <int P, bool DAG, bool C12, int LSC>
+// FP32 / FP16 / BF16: one thread per (site, slice pair), packed two-wide arithmetic. EPI = false
+// compiles the kernel without the epilogue (pre = post = none).
+template <int P, bool DAG, bool C12, int LSC, bool EPI>
 __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
   using T = typename Store<P>::T;
   constexpr int LB = link_bytes(sizeof(T), C12);
@@ -514,8 +648,13 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
   const int tid = threadIdx.x;
   const int site_local = tid / Lsh;
   const int q = tid - site_local * Lsh;
-  const int site = blockIdx.x * a.sites_per_cta + site_local;
-  const bool active = site_local < a.sites_per_cta && site < a.g.N4h;
+  // Every launch has exactly threads-per-site x sites_per_cta threads (dhop_half), so only the
+  // last CTA can hold threads past the end of the lattice. They run the same straight-line code
+  // on the last site (a valid address) and store nothing: a guard around the hop loop instead
+  // measured 5-7% slower.
+  const int site_raw = blockIdx.x * a.sites_per_cta + site_local;
+  const bool active = site_raw < a.g.N4h;
+  const int site = active ? site_raw : a.g.N4h - 1;
   const size_t site_bytes = (size_t)Lsh * 2 * 24 * sizeof(T);
   const float alpha = (float)a.alpha;
 
@@ -523,71 +662,73 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
 #pragma unroll
   for (int r = 0; r < 24; ++r) acc[r] = make_float2(0.f, 0.f);
 
-  // The eight links of each site, staged once per CTA: thread q of a site fetches the links of
-  // hops q, q + Lsh, ... (hop h = 2 mu + backward), so every link is requested from memory once
-  // instead of once per slice pair; the hops then read them from shared memory.
-  constexpr bool STAGE = dhop_stage_links(P);
+  // The eight links of each site, staged once per CTA as FP32: thread q of a site fetches the
+  // links of hops q, q + Lsh, ... (hop h = 2 mu + backward), so every link is requested from
+  // memory once instead of once per slice pair; the hops then read them from shared memory.
+  constexpr int LSS = dhop_link_site_bytes(P, C12);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  char* lsm = reinterpret_cast<char*>(smem_raw);  // [site_local][hop 8][LB]
+  char* lsm = reinterpret_cast<char*>(smem_raw) + (size_t)site_local * LSS;  // [hop 8][80 bytes]
   const char* Uo = static_cast<const char*>(a.Uout);
   const char* Ui = static_cast<const char*>(a.Uin);
-  int c[4];
-  if (active) cb_coords(a.g, site, a.out_parity, c);
-  if (STAGE) {
-    if (active) {
-      for (int h = q; h < 8; h += Lsh) {
-        const int mu = h >> 1;
-        const char* src;
-        if ((h & 1) == 0) {
-          src = Uo + ((size_t)site * 4 + mu) * LB;
-        } else {
-          int ph;
-          src = Ui + ((size_t)cb_neighbour(a.g, site, c, mu, false, ph) * 4 + mu) * LB;
-        }
-        copy_link<P, C12>(lsm + ((size_t)site_local * 8 + h) * LB, src);
-      }
+  // Neighbour indices and boundary phases of the eight hops, all computed before the first load
+  // so that the hop loop below is straight-line code whose loads the compiler can issue early.
+  int nb[8], phs[8];
+  {
+    int c[4];
+    cb_coords(a.g, site, a.out_parity, c);
+#pragma unroll
+    for (int h = 0; h < 8; ++h) nb[h] = cb_neighbour(a.g, site, c, h >> 1, (h & 1) == 0, phs[h]);
+    for (int h = q; h < 8; h += Lsh) {
+      const int mu = h >> 1;
+      const char* src = (h & 1) == 0 ? Uo + ((size_t)site * 4 + mu) * LB : Ui + ((size_t)nb[h] * 4 + mu) * LB;
+      stage_link_f32<P, C12>(lsm + h * DHOP_LINK_F32_BYTES, src);
     }
-    __syncthreads();
   }
+  __syncthreads();
 
-  if (active) {
+  {
     const char* in = static_cast<const char*>(a.in);
 #pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-      {  // forward hop: (1 + SF gamma_mu) U_mu(x) psi(x + mu)
-        int ph;
-        const int j = cb_neighbour(a.g, site, c, mu, true, ph);
-        float u[18];
-        if (STAGE)
-          load_link_smem<P, C12>(lsm + ((size_t)site_local * 8 + 2 * mu) * LB, u);
+    for (int hop = 0; hop < 8; ++hop) {
+      // hop = 2 mu: forward, (1 + SF gamma_mu) U_mu(x) psi(x + mu);
+      // hop = 2 mu + 1: backward, (1 + SB gamma_mu) U_mu(x - mu)^+ psi(x - mu).
+      // The neighbour's vectors are requested first, the link is read from shared memory after.
+      const int mu = hop >> 1;
+      const bool fwd = (hop & 1) == 0;
+      float2 h[12], uh[12];
+      float u[18];
+      const char* nbp = in + (size_t)nb[hop] * site_bytes;
+      if constexpr (P == P32) {
+        float2 psi[24];
+        load_pair<P, LSHC>(nbp, q, Lsh, psi);
+        load_link_f32(lsm + hop * DHOP_LINK_F32_BYTES, u);
+        if (fwd)
+          project2<SF>(mu, psi, h);
         else
-          load_link<P, C12>(Uo + ((size_t)site * 4 + mu) * LB, u);
-        float2 psi[24], h[12], uh[12];
-        load_pair<P, LSHC>(in + (size_t)j * site_bytes, q, Lsh, psi);
-        project2<SF>(mu, psi, h);
-        su3_mul2<false>(u, h, uh);
-        accumulate2<SF>(mu, uh, ph < 0 ? -alpha : alpha, acc);
+          project2<SB>(mu, psi, h);
+      } else {
+        uint32_t w[24];
+        load_words<P, LSHC>(nbp, q, Lsh, w);
+        load_link_f32(lsm + hop * DHOP_LINK_F32_BYTES, u);
+        if (fwd)
+          project2w<P, SF>(mu, w, h);
+        else
+          project2w<P, SB>(mu, w, h);
       }
-      {  // backward hop: (1 + SB gamma_mu) U_mu(x - mu)^+ psi(x - mu)
-        int ph;
-        const int j = cb_neighbour(a.g, site, c, mu, false, ph);
-        float u[18];
-        if (STAGE)
-          load_link_smem<P, C12>(lsm + ((size_t)site_local * 8 + 2 * mu + 1) * LB, u);
-        else
-          load_link<P, C12>(Ui + ((size_t)j * 4 + mu) * LB, u);
-        float2 psi[24], h[12], uh[12];
-        load_pair<P, LSHC>(in + (size_t)j * site_bytes, q, Lsh, psi);
-        project2<SB>(mu, psi, h);
+      const float cph = phs[hop] < 0 ? -alpha : alpha;
+      if (fwd) {
+        su3_mul2<false>(u, h, uh);
+        accumulate2<SF>(mu, uh, cph, acc);
+      } else {
         su3_mul2<true>(u, h, uh);
-        accumulate2<SB>(mu, uh, ph < 0 ? -alpha : alpha, acc);
+        accumulate2<SB>(mu, uh, cph, acc);
       }
     }
   }
 
   // ------------------------------------------------------------ epilogue
   char* outb = static_cast<char*>(a.out) + (size_t)site * site_bytes;
-  if (active && a.pre != PRE_NONE) {
+  if (EPI && active && a.pre != PRE_NONE) {
     const char* auxb = static_cast<const char*>(a.aux) + (size_t)site * site_bytes;
     const float2 B = f2((float)a.beta);
     if (a.pre == PRE_AUX) {
@@ -609,7 +750,7 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
     }
   }
   const bool pad_lane = (Ls & 1) && q == Lsh - 1;  // slice 2q+1 is the zero pad
-  if (a.post == POST_NONE) {
+  if (!EPI || a.post == POST_NONE) {
     if (active) {
       if (pad_lane) {
 #pragma unroll
@@ -621,7 +762,7 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
   }
   // Fifth-dimension inverse through shared memory (after the staged links): whole sites live in
   // this CTA.
-  float* sm = reinterpret_cast<float*>(smem_raw + (STAGE ? dhop_link_smem_bytes(a.sites_per_cta, LB) : 0));
+  float* sm = reinterpret_cast<float*>(smem_raw + dhop_link_smem_bytes(P, a.sites_per_cta, C12));
   if (active) {
     float* d0 = sm + ((size_t)site_local * Ls + 2 * q) * 24;
 #pragma unroll
@@ -743,7 +884,7 @@ __device__ __forceinline__ void dhop_body_lane64(const DhopArgs& a) {
     }
     return;
   }
-  double* sm = reinterpret_cast<double*>(smem_raw + dhop_link_smem_bytes(a.sites_per_cta, LB));
+  double* sm = reinterpret_cast<double*>(smem_raw + dhop_link_smem_bytes(P64, a.sites_per_cta, C12));
   if (active && !pad) {
     double* dst = sm + ((size_t)site_local * Ls + s) * 24;
 #pragma unroll
@@ -773,12 +914,14 @@ __device__ __forceinline__ void dhop_body_lane64(const DhopArgs& a) {
   }
 }
 
-// Register budget: at most 256 threads per CTA and two such CTAs per SM (128 registers per
-// thread) for the packed FP32 and 16-bit kernels; the FP64 kernel is bound by the FP64 pipe and
-// keeps more registers instead.
+// Register budget. Every launch of dhop_kernel has at most 128 threads (128 / threads-per-site
+// whole sites). The packed kernels keep four such CTAs per SM (128 registers per thread), except
+// FP16 storage, measured fastest with three (168 registers: its mixed-precision projection keeps
+// more values live); the FP64 kernel is bound by the FP64 pipe and keeps more registers instead.
 template <int P>
 struct DhopOccupancy {
-  static constexpr int MIN_BLOCKS = (P == P64) ? 1 : 2;
+  static constexpr int THREADS = 128;
+  static constexpr int MIN_BLOCKS = (P == P64) ? 1 : (P == P16) ? 3 : 4;
 };
 
 // Threads per site: slice pairs (packed kernels) or padded slices (FP64).
@@ -788,12 +931,12 @@ inline int dhop_threads_per_site(int prec, int Ls) { return prec == P64 ? ls_pad
 #define DWF_LS_SPECIALISATIONS(M) M(8) M(12) M(16) M(24) M(32)
 inline bool dhop_ls_specialised(int Ls) { return Ls == 8 || Ls == 12 || Ls == 16 || Ls == 24 || Ls == 32; }
 
-template <int P, bool DAG, bool C12, int LSC>
-__global__ void __launch_bounds__(256, DhopOccupancy<P>::MIN_BLOCKS) dhop_kernel(const __grid_constant__ DhopArgs a) {
+template <int P, bool DAG, bool C12, int LSC, bool EPI>
+__global__ void __launch_bounds__(DhopOccupancy<P>::THREADS, DhopOccupancy<P>::MIN_BLOCKS) dhop_kernel(const __grid_constant__ DhopArgs a) {
   if constexpr (P == P64)
     dhop_body_lane64<DAG, C12, LSC>(a);
   else
-    dhop_body_pair<P, DAG, C12, LSC>(a);
+    dhop_body_pair<P, DAG, C12, LSC, EPI>(a);
 }
 
 // Host-side launcher, instantiated once per storage precision in its own translation unit.

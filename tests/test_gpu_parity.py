@@ -134,7 +134,7 @@ def test_dhop_low_precision_storage(dwf, oracle_lib, prec, dims, Ls):
         assert rel(out, ref_exact) < 4 * TOL[prec]
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_dhop_compressed_links(dwf, oracle_lib, prec):
     dims, Ls = (4, 4, 6, 4), 6
     op, U = make(dwf, dims, Ls, 31, compress12=True)
@@ -142,7 +142,7 @@ def test_dhop_compressed_links(dwf, oracle_lib, prec):
     f = op.pack(dev(psi), prec, dwf.FULL)
     out = host(op.unpack(op.dhop(f, dwf.FULL)))
     ref = oracle_lib.dhop(dims, Ls, BC, U, psi)
-    tol = {0: 1e-12, 1: 1e-5, 2: 4 * TOL[2]}[prec]
+    tol = {0: 1e-12, 1: 1e-5, 2: 4 * TOL[2], 3: 4 * TOL[3]}[prec]
     assert rel(out, ref) < tol
 
 
@@ -177,7 +177,7 @@ def test_mooee_family(dwf, oracle_lib, Ls, prec):
 
 
 @pytest.mark.parametrize("dims,Ls", [((4, 4, 4, 4), 8), ((2, 4, 6, 4), 5), ((6, 4, 2, 2), 12)])
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_m_mpc_mdagm(dwf, oracle_lib, dims, Ls, prec):
     op, U = make(dwf, dims, Ls, 61)
     psi = synth.random_spinor(dims, Ls, seed=62)
@@ -375,87 +375,6 @@ def test_staged_cg_fp16(dwf, oracle_lib, staged):
     assert st.converged and st.true_residual <= 1e-10
     r = b - oracle_lib.m(dims, Ls, M5, MASS, BC, U, host(op.unpack(x)))
     assert np.linalg.norm(r) / np.linalg.norm(b) < 1e-8
-
-
-# ---------------------------------------------------------------- pipelined persistent kernel
-# With GRID_DWF_PIPE=1 at handle creation, the FP32 and 16-bit precisions with Ls in
-# {8, 12, 16, 24, 32} run the pipelined kernel: tiles of R whole x-rows (R = 1 streams Y+ and
-# Y- separately, R >= 2 reads the interior y-neighbours from the tile's own rows plus two halo
-# rows; R = Ly makes the halo rows wrap into the tile), neighbour rows streamed through a ring of
-# shared-memory slots, links one tile ahead.
-
-
-@pytest.fixture
-def pipe(monkeypatch):
-    monkeypatch.setenv("GRID_DWF_PIPE", "1")
-
-
-PIPE_CASES = [((8, 4, 4, 6), 8), ((16, 4, 2, 4), 16), ((24, 2, 2, 4), 12), ((8, 2, 4, 2), 16), ((32, 2, 2, 2), 8),
-              ((16, 2, 2, 2), 32), ((8, 6, 4, 2), 8), ((4, 4, 4, 4), 8)]
-
-
-@pytest.mark.parametrize("dims,Ls", PIPE_CASES)
-@pytest.mark.parametrize("prec", [1, 2, 3])
-def test_pipe_dhop_parity(dwf, oracle_lib, pipe, dims, Ls, prec):
-    op, U = make(dwf, dims, Ls, 171, eps=0.3)
-    psi = synth.random_spinor(dims, Ls, seed=172)
-    f = op.pack(dev(psi), prec, dwf.FULL)
-    for dag in (False, True):
-        ref = oracle_lib.dhop(dims, Ls, BC, round_spinor(U, prec), round_spinor(psi, prec), dag=dag)
-        out = host(op.unpack(op.dhop(f, dwf.FULL, dag=dag)))
-        assert rel(out, ref) < TOL[prec], (dag, rel(out, ref))
-
-
-@pytest.mark.parametrize("dims,Ls", PIPE_CASES)
-@pytest.mark.parametrize("prec", [1, 2])
-def test_pipe_compressed_and_epilogues(dwf, oracle_lib, pipe, dims, Ls, prec):
-    tol = TOL[prec]
-    op, U = make(dwf, dims, Ls, 181, compress12=True)
-    psi = synth.random_spinor(dims, Ls, seed=182)
-    psi_r = round_spinor(psi, prec)
-    f = op.pack(dev(psi), prec, dwf.FULL)
-    assert rel(host(op.unpack(op.dhop(f, dwf.FULL))), oracle_lib.dhop(dims, Ls, BC, round_spinor(U, prec), psi_r)) < tol
-    op2, U2 = make(dwf, dims, Ls, 183)
-    f2 = op2.pack(dev(psi), prec, dwf.FULL)
-    U_r = round_spinor(U2, prec)
-    for dag in (False, True):
-        out = host(op2.unpack(op2.m(f2, dag=dag)))
-        assert rel(out, oracle_lib.m(dims, Ls, M5, MASS, BC, U_r, psi_r, dag=dag)) < tol
-    _, po = parity_fields(oracle_lib, dims, psi_r)
-    fo = op2.pack(dev(po), prec, dwf.ODD)
-    mask = oracle_lib.parity_mask(dims)
-    for dag in (False, True):
-        out = host(op2.unpack(op2.mpc(fo, dag=dag), subset=dwf.ODD))
-        ref = oracle_lib.mpc(dims, Ls, M5, MASS, BC, U_r, po, dag=dag)
-        assert rel(out[mask], ref[mask]) < 8 * tol
-    out = host(op2.unpack(op2.mdagm(fo), subset=dwf.ODD))
-    ref = oracle_lib.mdagm(dims, Ls, M5, MASS, BC, U_r, po)
-    assert rel(out[mask], ref[mask]) < 8 * tol
-
-
-def test_pipe_cg_mixed(dwf, oracle_lib, pipe):
-    dims, Ls = (8, 4, 4, 4), 8
-    op, U = make(dwf, dims, Ls, 191, eps=0.4)
-    b = synth.random_spinor(dims, Ls, seed=192)
-    for mode in (dwf.CG_MIXED_FP32, dwf.CG_MIXED_FP16, dwf.CG_MIXED_BF16):
-        x, st = op.cg(op.pack(dev(b), 0, dwf.FULL), tol=1e-10, maxiter=5000, mode=mode)
-        assert st.converged and st.true_residual <= 1e-10
-        r = b - oracle_lib.m(dims, Ls, M5, MASS, BC, U, host(op.unpack(x)))
-        assert np.linalg.norm(r) / np.linalg.norm(b) < 1e-8
-
-
-@pytest.mark.parametrize("prec", [1, 2, 3])
-def test_pipe_full_size_16x16x16x16_ls16(dwf, oracle_lib, pipe, prec):
-    w = _workload("dwf_16x16x16x16_ls16_exp0.3")
-    dims, Ls = w["dims"], w["Ls"]
-    U = synth.random_gauge(dims, seed=1000 * w["case"], eps=w["eps"])
-    psi = synth.random_spinor(dims, Ls, seed=1000 * w["case"] + 1)
-    op = dwf.GridDWF(dims, Ls, w["M5"], w["mass"], bc=BC)
-    op.set_gauge(dev(U))
-    f = op.pack(dev(psi), prec, dwf.FULL)
-    out = host(op.unpack(op.dhop(f, dwf.FULL)))
-    ref = oracle_lib.dhop(dims, Ls, BC, round_spinor(U, prec), round_spinor(psi, prec))
-    assert rel(out, ref) < TOL[prec]
 
 
 # ---------------------------------------------------------------- full-size workloads
