@@ -64,6 +64,9 @@ def _load():
             lib.dwf_oracle_force.argtypes = [_ip, ctypes.c_int, ctypes.c_double, ctypes.c_double, _ip, _dp, _dp,
                                              _dp, _dp, ctypes.c_int]
             lib.dwf_oracle_force.restype = ctypes.c_double
+            lib.dwf_oracle_pf_force.argtypes = [_ip, ctypes.c_int, ctypes.c_double, ctypes.c_double, _ip, _dp, _dp,
+                                                _dp, _dp, _dp, ctypes.c_double, ctypes.c_int, _dp, ctypes.c_int]
+            lib.dwf_oracle_pf_force.restype = ctypes.c_int
             lib.dwf_oracle_norm2.argtypes = [ctypes.c_long, _dp]
             lib.dwf_oracle_norm2.restype = ctypes.c_double
             _lib = lib
@@ -187,6 +190,26 @@ def force(dims, Ls, M5, mass, bc, U, psi, nthreads=None):
     S = _load().dwf_oracle_force(_ints(dims), Ls, M5, mass, _ints(bc), _ptr(U), _ptr(psi), _ptr(F), _ptr(G),
                                  nthreads or default_threads())
     return S, F, G
+
+
+def pf_force(dims, Ls, M5, mass, bc, U, phi, tol=1e-12, maxiter=100000, want_force=True, nthreads=None):
+    """Pseudofermion action S = phi^+ (Mpc^+ Mpc)^-1 phi (odd sites of phi) and its link derivatives.
+
+    Returns (S, X, F, G, iterations): X = (Mpc^+ Mpc)^-1 phi on odd sites (zero on even), F the su(3)
+    force and G = dS/dRe U + i dS/dIm U in the gauge layout (None unless want_force); iterations
+    is -1 if CG did not reach tol within maxiter.
+    """
+    U, phi = _c128(U), _c128(phi)
+    _check_spinor(dims, Ls, phi)
+    X = np.zeros_like(phi)
+    F = np.empty_like(U) if want_force else None
+    G = np.empty_like(U) if want_force else None
+    S = ctypes.c_double(0.0)
+    null = ctypes.POINTER(ctypes.c_double)()
+    it = _load().dwf_oracle_pf_force(_ints(dims), Ls, M5, mass, _ints(bc), _ptr(U), _ptr(phi), _ptr(X),
+                                     _ptr(F) if want_force else null, _ptr(G) if want_force else null, tol,
+                                     int(maxiter), ctypes.byref(S), nthreads or default_threads())
+    return S.value, X, F, G, it
 
 
 def norm2(v) -> float:

@@ -553,3 +553,151 @@ double dwf_oracle_force(const int dims[4], int Ls, double M5, double mass, const
   free(chi);
   return S;
 }
+
+/*
+ * Two-flavour pseudofermion action on odd sites, S = phi^+ (Mpc^+ Mpc)^-1 phi, and its
+ * derivative with respect to the links (the survey's next-step row: the operator used inside
+ * hybrid Monte Carlo, differentiated through the solve).
+ *
+ * X = (Mpc^+ Mpc)^-1 phi by plain conjugate gradients from X = 0, stopping when the recursive
+ * residual satisfies |r| <= tol |phi|; S = Re phi^+ X; Y = Mpc X. Only the hopping blocks of Mpc
+ * depend on the links:
+ *   d(Mpc^+ Mpc) = dMpc^+ Mpc + Mpc^+ dMpc,  so  dS = -X^+ d(Mpc^+ Mpc) X = -2 Re Y^+ dMpc X,
+ *   dMpc = -dMoe Mooee^-1 Meo - Moe Mooee^-1 dMeo = -(1/4)(dD_oe Mooee^-1 D_eo + D_oe Mooee^-1 dD_eo),
+ * which gives dS = (1/2) Re B^+ dD A for the full fields
+ *   A = Mooee^-1 D_eo X on even sites and X on odd sites,
+ *   B = Mooee^-+ (D_oe)^+ Y on even sites and Y on odd sites   ((D_oe)^+ = the adjoint hop from odd to even).
+ * Per link U_mu(x), with phase the boundary factor of the hop x -> x+mu, the functional
+ * Re B^+ D A contains U_mu(x) through Re B(x)^+ (1 - gamma_mu) U A(x+mu) and through
+ * Re B(x+mu)^+ (1 + gamma_mu) U^+ A(x), so with the colour outer products
+ *   W1 = sum_{s,spin} A(x+mu) (x) [(1 - gamma_mu) B(x)]^+,   W2 = sum_{s,spin} A(x) (x) [(1 + gamma_mu) B(x+mu)]^+
+ * its ambient gradient is phase (W1^+ + W2) and its su(3) force (U -> exp(eps T) U) is
+ * TA(phase (-U W1 + W2 U^+)); S takes half of each:
+ *   G = dS/dRe U + i dS/dIm U = (1/2) phase (W1^+ + W2),   F = (1/2) TA(phase (-U W1 + W2 U^+)).
+ * X (odd sites) receives the solution; F and G may be NULL. Returns the number of CG iterations,
+ * or -1 if maxiter was reached first; *S_out receives S.
+ */
+int dwf_oracle_pf_force(const int dims[4], int Ls, double M5, double mass, const int bc[4], const double* Ud,
+                        const double* phid, double* Xd, double* Fd, double* Gd, double tol, int maxiter,
+                        double* S_out, int nthreads) {
+  const geom_t g = make_geom(dims, Ls, bc);
+  const long n = g.V * Ls * 12;
+  const cplx* phi = (const cplx*)phid;
+  cplx* X = (cplx*)Xd;
+  cplx* r = (cplx*)calloc(n, sizeof(cplx));
+  cplx* p = (cplx*)calloc(n, sizeof(cplx));
+  cplx* Ap = (cplx*)calloc(n, sizeof(cplx));
+  cplx* A = (cplx*)calloc(n, sizeof(cplx));
+  cplx* B = (cplx*)calloc(n, sizeof(cplx));
+  cplx* t = (cplx*)calloc(n, sizeof(cplx));
+  /* CG on Mpc^+ Mpc X = phi, odd sites */
+  for (long i = 0; i < n; ++i) {
+    X[i] = 0;
+    r[i] = phi[i];
+  }
+  zero_parity(&g, r, 0);
+  memcpy(p, r, sizeof(cplx) * n);
+  const double phi_norm = sqrt(norm2(n, r));
+  double rr = norm2(n, r);
+  int k = 0;
+  while (sqrt(rr) > tol * phi_norm) {
+    if (k >= maxiter) {
+      k = -1;
+      break;
+    }
+    dwf_oracle_mdagm(dims, Ls, M5, mass, bc, Ud, (const double*)p, (double*)Ap, nthreads);
+    const double alpha = rr / creal(inner(n, p, Ap));
+    for (long i = 0; i < n; ++i) {
+      X[i] += alpha * p[i];
+      r[i] -= alpha * Ap[i];
+    }
+    const double rr_new = norm2(n, r);
+    const double beta = rr_new / rr;
+    rr = rr_new;
+    for (long i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
+    ++k;
+  }
+  *S_out = creal(inner(n, phi, X));
+  /* A: X on odd sites, Mooee^-1 D_eo X on even sites */
+  dwf_oracle_dhop(dims, Ls, bc, Ud, (const double*)X, (double*)t, 0, 0, nthreads);
+  dwf_oracle_mooee(dims, Ls, M5, mass, (const double*)t, (double*)A, 0, 1, nthreads);
+  /* B: Y = Mpc X on odd sites, Mooee^-+ (D_oe)^+ Y on even sites */
+  dwf_oracle_mpc(dims, Ls, M5, mass, bc, Ud, (const double*)X, (double*)Ap, 0, nthreads);
+  dwf_oracle_dhop(dims, Ls, bc, Ud, (const double*)Ap, (double*)t, 0, 1, nthreads);
+  dwf_oracle_mooee(dims, Ls, M5, mass, (const double*)t, (double*)B, 1, 1, nthreads);
+  for (long xs = 0; xs < g.V; ++xs) {
+    int c[4];
+    site_coords(&g, xs, c);
+    if (site_parity(c) == 1)
+      for (int i = 0; i < Ls * 12; ++i) {
+        A[xs * Ls * 12 + i] = X[xs * Ls * 12 + i];
+        B[xs * Ls * 12 + i] = Ap[xs * Ls * 12 + i];
+      }
+  }
+  cplx gam[5][4][4];
+  gamma_matrices(gam);
+  const cplx* U = (const cplx*)Ud;
+  cplx* F = (cplx*)Fd;
+  cplx* G = (cplx*)Gd;
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+  for (long x = 0; x < g.V; ++x) {
+    int c[4];
+    site_coords(&g, x, c);
+    for (int mu = 0; mu < 4; ++mu) {
+      int cn[4] = {c[0], c[1], c[2], c[3]};
+      cn[mu] = (c[mu] + 1) % g.L[mu];
+      const long xf = lex_index(&g, cn);
+      const double phase = c[mu] == g.L[mu] - 1 ? g.bc[mu] : 1.0;
+      cplx W1[9] = {0}, W2[9] = {0};
+      for (int s = 0; s < Ls; ++s) {
+        const cplx* a_x = A + (x * Ls + s) * 12;
+        const cplx* a_f = A + (xf * Ls + s) * 12;
+        const cplx* b_x = B + (x * Ls + s) * 12;
+        const cplx* b_f = B + (xf * Ls + s) * 12;
+        cplx pb_x[12], pb_f[12]; /* (1 - gamma_mu) B(x), (1 + gamma_mu) B(x+mu) */
+        for (int sp = 0; sp < 4; ++sp)
+          for (int a = 0; a < 3; ++a) {
+            cplx gx = 0, gf = 0;
+            for (int sq = 0; sq < 4; ++sq) {
+              gx += gam[mu][sp][sq] * b_x[sq * 3 + a];
+              gf += gam[mu][sp][sq] * b_f[sq * 3 + a];
+            }
+            pb_x[sp * 3 + a] = b_x[sp * 3 + a] - gx;
+            pb_f[sp * 3 + a] = b_f[sp * 3 + a] + gf;
+          }
+        for (int sp = 0; sp < 4; ++sp)
+          for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+              W1[a * 3 + b] += a_f[sp * 3 + a] * conj(pb_x[sp * 3 + b]);
+              W2[a * 3 + b] += a_x[sp * 3 + a] * conj(pb_f[sp * 3 + b]);
+            }
+      }
+      const cplx* u = U + (x * 4 + mu) * 9;
+      if (F) {
+        cplx Z[9], ta[9];
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) {
+            cplx uW1 = 0, W2ud = 0;
+            for (int q = 0; q < 3; ++q) {
+              uW1 += u[a * 3 + q] * W1[q * 3 + b];
+              W2ud += W2[a * 3 + q] * conj(u[b * 3 + q]);
+            }
+            Z[a * 3 + b] = phase * (-uW1 + W2ud);
+          }
+        traceless_antihermitian(Z, ta);
+        for (int i = 0; i < 9; ++i) F[(x * 4 + mu) * 9 + i] = 0.5 * ta[i];
+      }
+      if (G)
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b)
+            G[(x * 4 + mu) * 9 + a * 3 + b] = 0.5 * phase * (conj(W1[b * 3 + a]) + W2[a * 3 + b]);
+    }
+  }
+  free(r);
+  free(p);
+  free(Ap);
+  free(A);
+  free(B);
+  free(t);
+  return k;
+}

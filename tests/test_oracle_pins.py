@@ -5,7 +5,8 @@ pinned by: dense brute-force matrices built independently (tests/_dense.py), the
 plane-wave closed form, gamma5- and gamma5*R5-hermiticity, adjoint identities, gauge
 covariance, the closed-form inverse of the fifth-dimension matrix, the determinant of the
 free zero-momentum operator (bare plus residual mass), exact dense solves, and central finite
-differences of the action.
+differences of the action (the action |M psi|^2 and the pseudofermion action
+phi^+ (Mpc^+ Mpc)^-1 phi, the latter against dense solves).
 """
 import numpy as np
 import pytest
@@ -319,6 +320,58 @@ def test_force_against_finite_differences(oracle_lib, dims, Ls, seed):
     Xa = 0.5 * (X - np.conj(np.swapaxes(X, -1, -2)))
     Xa = Xa - (np.trace(Xa, axis1=-2, axis2=-1) / 3.0)[..., None, None] * np.eye(3)
     assert rel(Xa, F) < 1e-13
+
+
+def _dense_pf_action(dims, Ls, U, phi):
+    """S = phi_o^+ (Mpc^+ Mpc)^-1 phi_o with Mpc from the blocks of the dense M, and the solution X."""
+    Mpc, o = _dense.dense_schur_odd(dims, Ls, M5, MASS, BC, U)
+    po = phi.ravel()[o]
+    xo = np.linalg.solve(Mpc.conj().T @ Mpc, po)
+    X = np.zeros(phi.size, dtype=complex)
+    X[o] = xo
+    return float(np.vdot(po, xo).real), X.reshape(phi.shape)
+
+
+@pytest.mark.parametrize("dims,Ls,seed", [((2, 2, 2, 4), 4, 501), ((4, 2, 2, 2), 3, 511)])
+def test_pf_action_and_solution_match_dense(oracle_lib, dims, Ls, seed):
+    U = synth.random_gauge(dims, seed=seed)
+    phi = synth.random_spinor(dims, Ls, seed=seed + 1)  # even sites are ignored
+    S, X, _, _, it = oracle_lib.pf_force(dims, Ls, M5, MASS, BC, U, phi, tol=1e-13, want_force=False)
+    S_ref, X_ref = _dense_pf_action(dims, Ls, U, phi)
+    assert it > 0
+    assert abs(S - S_ref) < 1e-10 * S_ref
+    assert rel(X, X_ref) < 1e-9
+    assert np.all(X[~oracle_lib.parity_mask(dims)] == 0)
+
+
+@pytest.mark.parametrize("dims,Ls,seed", [((2, 2, 2, 4), 4, 521), ((2, 4, 2, 2), 2, 531)])
+def test_pf_force_against_finite_differences(oracle_lib, dims, Ls, seed):
+    """F and G of S = phi^+ (Mpc^+ Mpc)^-1 phi against central differences of the dense action."""
+    U = synth.random_gauge(dims, seed=seed)
+    phi = synth.random_spinor(dims, Ls, seed=seed + 1)
+    S, _, F, G, _ = oracle_lib.pf_force(dims, Ls, M5, MASS, BC, U, phi, tol=1e-13)
+    action = lambda UU: _dense_pf_action(dims, Ls, UU, phi)[0]
+    assert np.allclose(F, -np.conj(np.swapaxes(F, -1, -2)), atol=1e-12 * np.abs(F).max())
+    assert np.allclose(np.trace(F, axis1=-2, axis2=-1), 0, atol=1e-12 * np.abs(F).max())
+    h = 1e-4  # central differences: truncation O(h^2) relative
+    for k in range(2):
+        A = synth.random_su3_algebra(U.shape[:-2], seed=seed + 10 + k)
+        fd = (action(_expm_su3(h * A) @ U) - action(_expm_su3(-h * A) @ U)) / (2 * h)
+        an = np.sum(np.einsum("...ba,...ba->...", np.conj(A), F).real)
+        assert abs(fd - an) < 1e-6 * (abs(an) + 1e-3 * S), (fd, an)
+    rng = np.random.default_rng(seed + 20)
+    for _ in range(2):
+        idx = tuple(int(rng.integers(0, n)) for n in U.shape)
+        for unit in (1.0, 1j):
+            E = np.zeros_like(U)
+            E[idx] = unit
+            fd = (action(U + h * E) - action(U - h * E)) / (2 * h)
+            an = (np.conj(G[idx]) * unit).real
+            assert abs(fd - an) < 1e-6 * (abs(an) + 1e-3 * S), (fd, an)
+    X = G @ np.conj(np.swapaxes(U, -1, -2))  # F = TA(G U^+)
+    Xa = 0.5 * (X - np.conj(np.swapaxes(X, -1, -2)))
+    Xa = Xa - (np.trace(Xa, axis1=-2, axis2=-1) / 3.0)[..., None, None] * np.eye(3)
+    assert rel(Xa, F) < 1e-12
 
 
 def test_psi_gradient_against_finite_differences(oracle_lib):
