@@ -353,6 +353,31 @@ def run_force(dwf, torch, spec, reps=20):
             "includes": "M psi (2 fused Dhop+Mooee launches), |M psi|^2, force and ambient-gradient kernel"}
 
 
+def run_pf_force(dwf, torch, spec):
+    """Pseudofermion action phi^+ (Mpc^+ Mpc)^-1 phi and its force on the 16^4 x 16 exp(0.3 i H)
+    workload: mixed-precision solve to a 1e-10 true residual, then the force contraction, per call
+    (FP64 plain solve for comparison)."""
+    dims, Ls = spec["dims"], spec["Ls"]
+    U = synth.random_gauge(dims, seed=1000 * spec["case"], eps=spec["eps"])
+    op = dwf.GridDWF(dims, Ls, spec["M5"], spec["mass"], bc=BC)
+    op.set_gauge(torch.from_numpy(U).cuda())
+    phi_c = synth.random_spinor(dims, Ls, seed=1000 * spec["case"] + 7)
+    phi = op.pack(torch.from_numpy(phi_c).cuda(), dwf.FP64, dwf.ODD)
+    out = {"workload": WORKLOAD, "tol": 1e-10}
+    for name, mode, prec in (("mixed_fp32_solve_fp32_force", dwf.CG_MIXED_FP32, dwf.FP32),
+                             ("fp64_solve_fp64_force", dwf.CG_FP64, dwf.FP64)):
+        op.pf_force(phi, tol=1e-6, mode=mode, precision=prec, raise_on_fail=False)  # warm-up: workspaces, links
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S, F, G, X, st = op.pf_force(phi, tol=1e-10, mode=mode, precision=prec, raise_on_fail=False)
+        torch.cuda.synchronize()
+        out[name] = {"seconds": round(time.perf_counter() - t0, 4), "iterations": st.iterations,
+                     "reliable_updates": st.reliable_updates, "true_residual": st.true_residual,
+                     "converged": st.converged, "S": S}
+    op.close()
+    return out
+
+
 def cpu_baseline_sample(spec, target_seconds=10.0):
     """The FP64 oracle as it stands, DhopEO + DhopOE on the full lattice, on all host cores."""
     import oracle
@@ -470,6 +495,7 @@ def gpu_arm(args):
         line["cg"] = run_cg(dwf, torch, synth.WORKLOADS[CG_WORKLOAD])
     if not args.no_force and rank == 0:
         line["force"] = run_force(dwf, torch, synth.WORKLOADS["dwf_16x16x16x16_ls16_haar"])
+        line["pf_force"] = run_pf_force(dwf, torch, spec)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline_sample(spec)
     barrier(world)
@@ -527,7 +553,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cg", action="store_true", help="skip the CG time-to-solution comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--no-force", action="store_true", help="skip the action/force timing")
+    ap.add_argument("--no-force", action="store_true", help="skip the action/force and pseudofermion force timing")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -145,6 +145,26 @@ int grid_dwf_cg(grid_dwf_t* h, const void* b, void* x, double tol, int maxiter, 
  * scratch. Under U -> exp(eps A) U with A in su(3): dS/deps = sum Re tr(A^+ F). *S_out on host. */
 int grid_dwf_force(grid_dwf_t* h, int precision, const void* psi, void* chi, double* F, double* G, double* S_out);
 
+/* Two-flavour pseudofermion action S = phi^+ (Mpc^+ Mpc)^-1 phi and its link derivative: the
+ * Schur normal operator above as it enters hybrid Monte Carlo, differentiated through the solve.
+ * The paper names no action; this is the next step after the operator, its solver and the force
+ * of |M psi|^2 (grid_dwf_force), and reuses all three.
+ *   phi        FP64 odd half field (device layout), the pseudofermion; read only.
+ *   X          FP64 odd half field: initial guess on input, X = (Mpc^+ Mpc)^-1 phi on output.
+ *   tol, maxiter, mode   as for grid_dwf_cg, applied to the FP64 true residual of
+ *              Mpc^+ Mpc X = phi (mixed modes: inner solve in FP32/FP16/BF16 storage).
+ *   precision  GRID_DWF_FP64 or GRID_DWF_FP32: arithmetic of the force contraction (FP32 fields
+ *              with FP64 accumulation, as in grid_dwf_force); the solve always returns FP64 X.
+ *   F, G       canonical gauge-layout FP64 device buffers (either may be NULL): the su(3) force
+ *              F (dS/deps = sum Re tr(A^+ F) under U -> exp(eps A) U) and G = dS/dRe U + i dS/dIm U.
+ *   S_out      host double receiving S = Re phi^+ X; stats as for grid_dwf_cg (may be NULL).
+ * With Y = Mpc X, dS = -2 Re Y^+ dMpc X = (1/2) Re B^+ dDhop A for the full fields
+ * A = (Mooee^-1 D_eo X, X) and B = (Mooee^-+ (D_oe)^+ Y, Y), contracted by the force kernel.
+ * Synchronises the handle's stream. Returns GRID_DWF_ERR_NOT_CONVERGED (X, F, G, S and stats
+ * still written) if tol is not reached within maxiter. */
+int grid_dwf_pf_force(grid_dwf_t* h, const void* phi, void* X, double tol, int maxiter, int mode, int precision,
+                      double* F, double* G, double* S_out, grid_dwf_cg_stats* stats);
+
 /* |a|^2 (b == NULL) or a^+ b with FP64 accumulation, like grid_dwf_norm2 / grid_dwf_inner, for
  * callers that cannot allocate device memory: code recording a CUDA graph (where cudaMalloc is
  * not allowed), loops that must not take cudaMalloc's implicit device synchronisation, or a host

@@ -14,7 +14,7 @@
 
 namespace gdwf {
 cudaError_t launch_force(int prec, bool c12, const Geom& g, const void* psi, const void* chi, const void* Ue,
-                         const void* Uo, double* F, double* G, cudaStream_t st);
+                         const void* Uo, double* F, double* G, double coef, cudaStream_t st);
 }
 
 using namespace gdwf;
@@ -60,6 +60,10 @@ enum WsId : int {
   WS_CG_TOS,
   WS_CG_TES,
   WS_CANON_TMP,
+  WS_PF_A,
+  WS_PF_B,
+  WS_PF_A32,
+  WS_PF_B32,
 };
 
 int fail(grid_dwf_t* h, int code, const std::string& msg) {
@@ -505,37 +509,36 @@ int grid_dwf_inner(grid_dwf_t* h, int precision, int subset, const void* a, cons
   return GRID_DWF_OK;
 }
 
-int grid_dwf_cg(grid_dwf_t* h, const void* b, void* x, double tol, int maxiter, int mode, grid_dwf_cg_stats* stats) {
-  if (!h) return GRID_DWF_ERR_INVALID_ARG;
-  if (mode < GRID_DWF_CG_FP64 || mode > GRID_DWF_CG_MIXED_BF16 || !(tol > 0) || maxiter < 0)
-    return fail(h, GRID_DWF_ERR_INVALID_ARG, "cg: bad mode/tol/maxiter");
-  RET(check_ptr(h, b, "b"));
-  RET(check_ptr(h, x, "x"));
+}  // extern "C"
+
+namespace {
+
+struct CgResult {
+  int iters = 0;
+  int updates = 0;
+  bool converged = false;
+  double true_res = 0;
+  double flops = 0;
+};
+
+// Solve Mpc^+ Mpc x_o = rhs for odd half fields in FP64 device layout, from the initial guess in
+// x_o, by plain FP64 CG or by FP64 defect correction around an inner CG in a lower storage
+// precision with reliable updates (mode). rhs is only read. Stops when the FP64 true residual
+// |rhs - Mpc^+ Mpc x_o| / |rhs| is at most tol, or after maxiter iterations; the true residual
+// is recomputed in FP64 at the end either way and returned with the counts.
+int cg_normal(grid_dwf_t* h, const void* rhs, void* xo_, double tol, int maxiter, int mode, CgResult& res) {
   const size_t hb = half_bytes(h, GRID_DWF_FP64);
-  if (overlap(b, 2 * hb, x, 2 * hb)) return fail(h, GRID_DWF_ERR_ALIAS, "cg: x overlaps b");
-  const auto t0 = std::chrono::steady_clock::now();
-  CK(cudaStreamSynchronize(h->stream), "cg start");
   const long N = h->g.N4h;
   const int Ls = h->Ls;
   const double half_flops = 1320.0 * (double)N * Ls;
   double flops = 0;
-  const char* be = static_cast<const char*>(b);
-  const char* bo = be + hb;
-  char* xe = static_cast<char*>(x);
-  char* xo = xe + hb;
-  void *te, *bp, *rhs, *r, *p, *Ap, *to;
+  char* xo = static_cast<char*>(xo_);
+  void *te, *r, *p, *Ap, *to;
   RET(ws_get(h, WS_CG_TE, hb, &te));
-  RET(ws_get(h, WS_CG_BP, hb, &bp));
-  RET(ws_get(h, WS_CG_RHS, hb, &rhs));
   RET(ws_get(h, WS_CG_R, hb, &r));
   RET(ws_get(h, WS_CG_AP, hb, &Ap));
   RET(ws_get(h, WS_CG_TO, hb, &to));
   const int P = GRID_DWF_FP64;
-  // Schur source: b'_o = b_o + D_oe Mooee^-1 b_e / 2; rhs = Mpc^+ b'_o
-  CK(launch_mooee(P, be, te, N, Ls, false, true, h->d5, h->mass, h->inv_d5, h->inv_den, h->stream), "cg source");
-  RET(dhop_half(h, P, te, bp, 1, false, PRE_AUX, POST_NONE, 0.5, 1.0, bo));
-  RET(mpc_impl(h, P, bp, rhs, true, te));
-  flops += 3 * half_flops;
   CK(launch_reduce(P, rhs, nullptr, N, Ls, h->partials, h->scal, FIN_STORE, S_TMP1, h->stream), "cg norm");
   // true residual r = rhs - A x_o
   RET(mdagm_impl(h, P, xo, Ap, to, te));
@@ -549,7 +552,6 @@ int grid_dwf_cg(grid_dwf_t* h, const void* b, void* x, double tol, int maxiter, 
   int iters = 0, updates = 0;
   bool converged = std::sqrt(rr) <= target;
   double true_res = rhs_norm > 0 ? std::sqrt(rr) / rhs_norm : 0.0;
-  int rc = GRID_DWF_OK;
 
   if (mode == GRID_DWF_CG_FP64) {
     RET(ws_get(h, WS_CG_P, hb, &p));
@@ -637,24 +639,62 @@ int grid_dwf_cg(grid_dwf_t* h, const void* b, void* x, double tol, int maxiter, 
   RET(mdagm_impl(h, P, xo, Ap, to, te));
   flops += 4 * half_flops;
   CK(launch_residual64(rhs, Ap, r, N, Ls, h->partials, h->scal, S_TMP0, h->stream), "cg final");
-  // x_e = Mooee^-1 (b_e + D_eo x_o / 2)
-  RET(dhop_half(h, P, xo, xe, 0, false, PRE_AUX, POST_INV, 0.5, 1.0, be));
-  flops += half_flops;
   RET(read_scalars(h));
   true_res = rhs_norm > 0 ? std::sqrt(h->host_scal[S_TMP0]) / rhs_norm : 0.0;
-  converged = true_res <= tol;
-  if (!converged) rc = fail(h, GRID_DWF_ERR_NOT_CONVERGED, "cg: tolerance not reached within maxiter");
+  res.iters = iters;
+  res.updates = updates;
+  res.true_res = true_res;
+  res.converged = true_res <= tol;
+  res.flops = flops;
+  return GRID_DWF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int grid_dwf_cg(grid_dwf_t* h, const void* b, void* x, double tol, int maxiter, int mode, grid_dwf_cg_stats* stats) {
+  if (!h) return GRID_DWF_ERR_INVALID_ARG;
+  if (mode < GRID_DWF_CG_FP64 || mode > GRID_DWF_CG_MIXED_BF16 || !(tol > 0) || maxiter < 0)
+    return fail(h, GRID_DWF_ERR_INVALID_ARG, "cg: bad mode/tol/maxiter");
+  RET(check_ptr(h, b, "b"));
+  RET(check_ptr(h, x, "x"));
+  const size_t hb = half_bytes(h, GRID_DWF_FP64);
+  if (overlap(b, 2 * hb, x, 2 * hb)) return fail(h, GRID_DWF_ERR_ALIAS, "cg: x overlaps b");
+  const auto t0 = std::chrono::steady_clock::now();
+  CK(cudaStreamSynchronize(h->stream), "cg start");
+  const long N = h->g.N4h;
+  const int Ls = h->Ls;
+  const double half_flops = 1320.0 * (double)N * Ls;
+  const char* be = static_cast<const char*>(b);
+  const char* bo = be + hb;
+  char* xe = static_cast<char*>(x);
+  char* xo = xe + hb;
+  void *te, *bp, *rhs;
+  RET(ws_get(h, WS_CG_TE, hb, &te));
+  RET(ws_get(h, WS_CG_BP, hb, &bp));
+  RET(ws_get(h, WS_CG_RHS, hb, &rhs));
+  const int P = GRID_DWF_FP64;
+  // Schur source: b'_o = b_o + D_oe Mooee^-1 b_e / 2; rhs = Mpc^+ b'_o
+  CK(launch_mooee(P, be, te, N, Ls, false, true, h->d5, h->mass, h->inv_d5, h->inv_den, h->stream), "cg source");
+  RET(dhop_half(h, P, te, bp, 1, false, PRE_AUX, POST_NONE, 0.5, 1.0, bo));
+  RET(mpc_impl(h, P, bp, rhs, true, te));
+  CgResult res;
+  RET(cg_normal(h, rhs, xo, tol, maxiter, mode, res));
+  // x_e = Mooee^-1 (b_e + D_eo x_o / 2)
+  RET(dhop_half(h, P, xo, xe, 0, false, PRE_AUX, POST_INV, 0.5, 1.0, be));
+  CK(cudaStreamSynchronize(h->stream), "cg end");
   const auto t1 = std::chrono::steady_clock::now();
   if (stats) {
-    stats->iterations = iters;
-    stats->reliable_updates = updates;
-    stats->converged = converged ? 1 : 0;
-    stats->true_residual = true_res;
+    stats->iterations = res.iters;
+    stats->reliable_updates = res.updates;
+    stats->converged = res.converged ? 1 : 0;
+    stats->true_residual = res.true_res;
     stats->seconds = std::chrono::duration<double>(t1 - t0).count();
-    stats->flops = flops;
+    stats->flops = res.flops + 4 * half_flops;
   }
-  if (rc == GRID_DWF_OK) RET(finish(h, "cg"));
-  return rc;
+  if (!res.converged) return fail(h, GRID_DWF_ERR_NOT_CONVERGED, "cg: tolerance not reached within maxiter");
+  return finish(h, "cg");
 }
 
 int grid_dwf_force(grid_dwf_t* h, int precision, const void* psi, void* chi, double* F, double* G, double* S_out) {
@@ -675,11 +715,80 @@ int grid_dwf_force(grid_dwf_t* h, int precision, const void* psi, void* chi, dou
      "force action");
   RET(ensure_gauge(h, precision));
   if (F || G)
-    CK(launch_force(precision, h->c12, h->g, psi, c, h->gauge[precision][0], h->gauge[precision][1], F, G, h->stream),
+    CK(launch_force(precision, h->c12, h->g, psi, c, h->gauge[precision][0], h->gauge[precision][1], F, G, 1.0,
+                    h->stream),
        "force");
   RET(read_scalars(h));
   if (S_out) *S_out = h->host_scal[S_TMP0];
   return finish(h, "force");
+}
+
+int grid_dwf_pf_force(grid_dwf_t* h, const void* phi, void* X, double tol, int maxiter, int mode, int precision,
+                      double* F, double* G, double* S_out, grid_dwf_cg_stats* stats) {
+  if (!h) return GRID_DWF_ERR_INVALID_ARG;
+  if (mode < GRID_DWF_CG_FP64 || mode > GRID_DWF_CG_MIXED_BF16 || !(tol > 0) || maxiter < 0)
+    return fail(h, GRID_DWF_ERR_INVALID_ARG, "pf_force: bad mode/tol/maxiter");
+  if (precision != GRID_DWF_FP64 && precision != GRID_DWF_FP32)
+    return fail(h, GRID_DWF_ERR_INVALID_ARG, "pf_force: precision must be FP64 or FP32");
+  RET(check_ptr(h, phi, "phi"));
+  RET(check_ptr(h, X, "X"));
+  const size_t hb = half_bytes(h, GRID_DWF_FP64);
+  if (overlap(phi, hb, X, hb)) return fail(h, GRID_DWF_ERR_ALIAS, "pf_force: X overlaps phi");
+  const size_t gb = (size_t)h->g.N4h * 2 * 4 * 18 * sizeof(double);
+  if (F && (overlap(F, gb, phi, hb) || overlap(F, gb, X, hb))) return fail(h, GRID_DWF_ERR_ALIAS, "pf_force: F overlaps");
+  if (G && (overlap(G, gb, phi, hb) || overlap(G, gb, X, hb))) return fail(h, GRID_DWF_ERR_ALIAS, "pf_force: G overlaps");
+  if (F && G && overlap(F, gb, G, gb)) return fail(h, GRID_DWF_ERR_ALIAS, "pf_force: F overlaps G");
+  const auto t0 = std::chrono::steady_clock::now();
+  CK(cudaStreamSynchronize(h->stream), "pf_force start");
+  const long N = h->g.N4h;
+  const int Ls = h->Ls;
+  const int P = GRID_DWF_FP64;
+  // X = (Mpc^+ Mpc)^-1 phi
+  CgResult res;
+  RET(cg_normal(h, phi, X, tol, maxiter, mode, res));
+  // Full fields A = (Mooee^-1 D_eo X, X) and B = (Mooee^-+ (D_oe)^+ Y, Y) with Y = Mpc X:
+  // dS = (1/2) Re B^+ dDhop A, i.e. -1/2 times the force kernel's bilinear.
+  void *A, *B;
+  RET(ws_get(h, WS_PF_A, 2 * hb, &A));
+  RET(ws_get(h, WS_PF_B, 2 * hb, &B));
+  char* Ae = static_cast<char*>(A);
+  char* Be = static_cast<char*>(B);
+  RET(mpc_impl(h, P, X, Be + hb, false, Ae));  // Ae = Mooee^-1 D_eo X, Bo = Mpc X
+  RET(dhop_half(h, P, Be + hb, Be, 0, true, PRE_NONE, POST_INV_DAG, 1.0, 0.0, nullptr));
+  CK(cudaMemcpyAsync(Ae + hb, X, hb, cudaMemcpyDeviceToDevice, h->stream), "pf_force copy");
+  // S = Re phi^+ X (phi^+ X is real for the Hermitian positive Mpc^+ Mpc)
+  CK(launch_reduce(P, phi, X, N, Ls, h->partials, h->scal, FIN_STORE, S_TMP0, h->stream), "pf_force action");
+  if (F || G) {
+    const void* a = A;
+    const void* b = B;
+    if (precision == GRID_DWF_FP32) {
+      const size_t fb32 = 2 * half_bytes(h, GRID_DWF_FP32);
+      void *a32, *b32;
+      RET(ws_get(h, WS_PF_A32, fb32, &a32));
+      RET(ws_get(h, WS_PF_B32, fb32, &b32));
+      CK(launch_convert(P, GRID_DWF_FP32, A, a32, 2 * N, Ls, nullptr, 1.0, h->stream), "pf_force convert");
+      CK(launch_convert(P, GRID_DWF_FP32, B, b32, 2 * N, Ls, nullptr, 1.0, h->stream), "pf_force convert");
+      a = a32;
+      b = b32;
+    }
+    RET(ensure_gauge(h, precision));
+    CK(launch_force(precision, h->c12, h->g, a, b, h->gauge[precision][0], h->gauge[precision][1], F, G, -0.5,
+                    h->stream),
+       "pf_force force");
+  }
+  RET(read_scalars(h));
+  if (S_out) *S_out = h->host_scal[S_TMP0];
+  const auto t1 = std::chrono::steady_clock::now();
+  if (stats) {
+    stats->iterations = res.iters;
+    stats->reliable_updates = res.updates;
+    stats->converged = res.converged ? 1 : 0;
+    stats->true_residual = res.true_res;
+    stats->seconds = std::chrono::duration<double>(t1 - t0).count();
+    stats->flops = res.flops + 3 * 1320.0 * (double)N * Ls;
+  }
+  if (!res.converged) return fail(h, GRID_DWF_ERR_NOT_CONVERGED, "pf_force: tolerance not reached within maxiter");
+  return finish(h, "pf_force");
 }
 
 }  // extern "C"

@@ -1,4 +1,7 @@
 // Derivative of the action S = |M psi|^2 with respect to the gauge links (the fermion force).
+// More generally the kernel differentiates the bilinear -Re chi^+ Dhop psi for any pair of full
+// fields (psi, chi), times a coefficient coef (1 for |M psi|^2 with chi = M psi, whose
+// variation is 2 Re chi^+ dM psi = -Re chi^+ dDhop psi; -1/2 for the pseudofermion action).
 //
 // With chi = M psi and M = Mooee - Dhop/2, only the hopping term depends on the links, so per
 // link U_mu(x), with phase the boundary factor of the hop x -> x + mu,
@@ -21,7 +24,7 @@ namespace gdwf {
 
 template <int P, bool C12>
 __global__ void __launch_bounds__(128) k_force(const Geom g, const char* psi, const char* chi, const char* Ue,
-                                               const char* Uo, double* F, double* G) {
+                                               const char* Uo, double* F, double* G, double coef) {
   using T = typename Store<P>::T;
   using R = typename Store<P>::R;
   constexpr int LB = link_bytes(sizeof(T), C12);
@@ -117,7 +120,7 @@ __global__ void __launch_bounds__(128) k_force(const Geom g, const char* psi, co
   double u[18];
 #pragma unroll
   for (int k = 0; k < 18; ++k) u[k] = (double)ur[k];
-  const double phd = (double)ph;
+  const double phd = coef * (double)ph;  // F and G are linear in the boundary phase and coef
   const long lex = c[0] + (long)g.L[0] * (c[1] + (long)g.L[1] * (c[2] + (long)g.L[2] * c[3]));
   double* Fo = F ? F + (lex * 4 + mu) * 18 : nullptr;
   double* Go = G ? G + (lex * 4 + mu) * 18 : nullptr;
@@ -167,7 +170,7 @@ __global__ void __launch_bounds__(128) k_force(const Geom g, const char* psi, co
 }
 
 cudaError_t launch_force(int prec, bool c12, const Geom& g, const void* psi, const void* chi, const void* Ue,
-                         const void* Uo, double* F, double* G, cudaStream_t st) {
+                         const void* Uo, double* F, double* G, double coef, cudaStream_t st) {
   const int threads = 128;
   const long links = 8L * g.N4h;
   const int blocks = (int)((links + threads - 1) / threads);
@@ -177,9 +180,9 @@ cudaError_t launch_force(int prec, bool c12, const Geom& g, const void* psi, con
   const char* o = static_cast<const char*>(Uo);
 #define FK(P_)                                                                   \
   if (c12)                                                                       \
-    k_force<P_, true><<<blocks, threads, 0, st>>>(g, ps, ch, e, o, F, G);        \
+    k_force<P_, true><<<blocks, threads, 0, st>>>(g, ps, ch, e, o, F, G, coef);        \
   else                                                                           \
-    k_force<P_, false><<<blocks, threads, 0, st>>>(g, ps, ch, e, o, F, G);
+    k_force<P_, false><<<blocks, threads, 0, st>>>(g, ps, ch, e, o, F, G, coef);
   switch (prec) {
     case P64: FK(P64) break;
     case P32: FK(P32) break;

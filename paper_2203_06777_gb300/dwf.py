@@ -96,6 +96,7 @@ def load(build: bool = True):
             "grid_dwf_inner": [vp, i, i, vp, vp, dp],
             "grid_dwf_cg": [vp, vp, vp, d, i, i, ctypes.POINTER(_CgStats)],
             "grid_dwf_force": [vp, i, vp, vp, vp, vp, dp],
+            "grid_dwf_pf_force": [vp, vp, vp, d, i, i, i, vp, vp, dp, ctypes.POINTER(_CgStats)],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -306,6 +307,29 @@ class GridDWF:
         return S.value, F, G
 
 
+    def pf_force(self, phi: torch.Tensor, x: torch.Tensor | None = None, tol=1e-10, maxiter=10000, mode=CG_FP64,
+                 precision=FP64, want_F=True, want_G=True, raise_on_fail=True):
+        """Pseudofermion action S = phi^+ (Mpc^+ Mpc)^-1 phi of an odd FP64 half field phi, with
+        its su(3) force F and ambient gradient G (canonical complex128, device) and the solution
+        X = (Mpc^+ Mpc)^-1 phi (odd FP64 half field). Returns (S, F, G, X, CgStats)."""
+        if self._check_field(phi) != FP64 or self._subset_of(phi) == FULL:
+            raise ValueError("pf_force needs an odd FP64 half field phi")
+        x = torch.zeros_like(phi) if x is None else x
+        lx, ly, lz, lt = self.dims
+        shape = (lt, lz, ly, lx, 4, 3, 3)
+        F = torch.empty(shape, dtype=torch.complex128, device=self.device) if want_F else None
+        G = torch.empty(shape, dtype=torch.complex128, device=self.device) if want_G else None
+        S = ctypes.c_double()
+        st = _CgStats()
+        self.lib.grid_dwf_set_stream(self._h, _ptr(torch.cuda.current_stream(self.device).cuda_stream))
+        rc = self.lib.grid_dwf_pf_force(self._h, _ptr(phi), _ptr(x), float(tol), int(maxiter), int(mode),
+                                        int(precision), _ptr(F), _ptr(G), ctypes.byref(S), ctypes.byref(st))
+        stats = CgStats(st.iterations, st.reliable_updates, bool(st.converged), st.true_residual, st.seconds, st.flops)
+        if rc != 0 and (raise_on_fail or rc != -4):
+            raise GridDWFError(rc, f"grid_dwf_pf_force: {self.lib.grid_dwf_last_error(self._h).decode()}")
+        return S.value, F, G, x, stats
+
+
 class DWFAction(torch.autograd.Function):
     """S = |M[U] psi|^2 with hand-written adjoints: dS/dpsi via M^+ (the library's dag kernels)
     and dS/dU via the force kernel. psi and U are canonical complex128 CUDA tensors; gradients
@@ -339,3 +363,30 @@ class DWFAction(torch.autograd.Function):
 
 def dwf_action(psi, U, op: GridDWF, prec=FP64):
     return DWFAction.apply(psi, U, op, prec)
+
+
+class PseudofermionAction(torch.autograd.Function):
+    """S = phi^+ (Mpc[U]^+ Mpc[U])^-1 phi for the odd sites of phi, differentiated through the
+    solve: dS/dU from the library's pseudofermion force (G), dS/dphi = 2 (Mpc^+ Mpc)^-1 phi
+    (odd sites). phi and U are canonical complex128 CUDA tensors; torch's convention for real
+    losses, dS/dRe z + i dS/dIm z."""
+
+    @staticmethod
+    def forward(ctx, phi, U, op: GridDWF, tol=1e-12, mode=CG_FP64):
+        op.set_gauge(U.detach())
+        f = op.pack(phi.detach(), FP64, ODD)
+        S, _, G, X, _ = op.pf_force(f, tol=tol, mode=mode, want_F=False, want_G=True)
+        ctx.save_for_backward(op.unpack(X, subset=ODD), G)
+        return torch.tensor(S, dtype=torch.float64, device=phi.device)
+
+    @staticmethod
+    def backward(ctx, gS):
+        X, G = ctx.saved_tensors
+        g = gS.to(torch.float64)
+        grad_phi = 2.0 * g * X if ctx.needs_input_grad[0] else None
+        grad_U = G * g if ctx.needs_input_grad[1] else None
+        return grad_phi, grad_U, None, None, None
+
+
+def pseudofermion_action(phi, U, op: GridDWF, tol=1e-12, mode=CG_FP64):
+    return PseudofermionAction.apply(phi, U, op, tol, mode)

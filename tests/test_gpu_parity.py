@@ -294,6 +294,86 @@ def test_autograd_gradcheck(dwf):
     assert torch.autograd.gradcheck(lambda p, u: dwf.dwf_action(p, u, op), (psi, U), eps=1e-6, atol=1e-5, rtol=1e-6)
 
 
+# ---------------------------------------------------------------- pseudofermion action and force
+# S = phi^+ (Mpc^+ Mpc)^-1 phi: the library solves to a true residual tol and contracts the
+# force; the oracle solves by plain CG to the same tol. Two solutions at residual tol differ by
+# at most cond(Mpc^+ Mpc) * tol relative (about 1e3 here), so X, F and G agree to 1e-8 at
+# tol = 1e-12, and S (quadratic in the error) much closer.
+
+
+def _odd(oracle, dims, psi):
+    return psi * oracle.parity_mask(dims)[..., None, None, None]
+
+
+@pytest.mark.parametrize("dims,Ls", [((4, 4, 4, 4), 8), ((2, 4, 2, 6), 3), ((4, 2, 4, 2), 16)])
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_pf_force_parity(dwf, oracle_lib, dims, Ls, mode):
+    op, U = make(dwf, dims, Ls, 201)
+    phi = _odd(oracle_lib, dims, synth.random_spinor(dims, Ls, seed=202))
+    f = op.pack(dev(phi), 0, dwf.ODD)
+    S, F, G, X, st = op.pf_force(f, tol=1e-12, mode=mode)
+    assert st.converged and st.true_residual <= 1e-12
+    S_ref, X_ref, F_ref, G_ref, it = oracle_lib.pf_force(dims, Ls, M5, MASS, BC, U, phi, tol=1e-12)
+    assert it > 0
+    assert abs(S - S_ref) < 1e-11 * S_ref
+    assert rel(host(op.unpack(X, subset=dwf.ODD)), X_ref) < 1e-8
+    assert rel(host(F), F_ref) < 1e-8
+    assert rel(host(G), G_ref) < 1e-8
+
+
+def test_pf_force_fp32_contraction(dwf, oracle_lib):
+    """FP32 force contraction of the FP64 solve: fields rounded once to FP32, FP64 accumulation."""
+    dims, Ls = (4, 4, 2, 4), 8
+    op, U = make(dwf, dims, Ls, 211)
+    phi = _odd(oracle_lib, dims, synth.random_spinor(dims, Ls, seed=212))
+    f = op.pack(dev(phi), 0, dwf.ODD)
+    S, F, G, X, st = op.pf_force(f, tol=1e-12, mode=dwf.CG_MIXED_FP32, precision=dwf.FP32)
+    S_ref, _, F_ref, G_ref, _ = oracle_lib.pf_force(dims, Ls, M5, MASS, BC, U, phi, tol=1e-12)
+    assert abs(S - S_ref) < 1e-11 * S_ref
+    assert rel(host(F), F_ref) < 2e-5
+    assert rel(host(G), G_ref) < 2e-5
+
+
+def test_pf_force_finite_differences_on_gpu(dwf, oracle_lib):
+    """The GPU force against central differences of the GPU action along su(3) directions."""
+    dims, Ls = (4, 4, 4, 4), 4
+    op, U = make(dwf, dims, Ls, 221)
+    phi = _odd(oracle_lib, dims, synth.random_spinor(dims, Ls, seed=222))
+    f = op.pack(dev(phi), 0, dwf.ODD)
+
+    def action(UU):
+        op.set_gauge(dev(UU))
+        return op.pf_force(f, tol=1e-13, maxiter=100000, want_F=False, want_G=False)[0]
+
+    S0 = action(U)
+    op.set_gauge(dev(U))
+    _, F, _, _, _ = op.pf_force(f, tol=1e-13, maxiter=100000, want_G=False)
+    F = host(F)
+    h = 1e-4
+    for k in range(2):
+        A = synth.random_su3_algebra(U.shape[:-2], seed=230 + k)
+        lam, v = np.linalg.eigh(-1j * h * A)
+        Ep = np.einsum("...ab,...b,...cb->...ac", v, np.exp(1j * lam), np.conj(v))
+        fd = (action(Ep @ U) - action(np.conj(np.swapaxes(Ep, -1, -2)) @ U)) / (2 * h)
+        an = np.sum(np.einsum("...ba,...ba->...", np.conj(A), F).real)
+        assert abs(fd - an) < 1e-6 * (abs(an) + 1e-3 * S0), (fd, an)
+
+
+def test_pf_autograd_matches_oracle(dwf, oracle_lib):
+    dims, Ls = (4, 2, 2, 4), 4
+    U = synth.random_gauge(dims, seed=241)
+    phi = _odd(oracle_lib, dims, synth.random_spinor(dims, Ls, seed=242))
+    op = dwf.GridDWF(dims, Ls, M5, MASS, bc=BC)
+    pt = dev(phi).requires_grad_(True)
+    Ut = dev(U).requires_grad_(True)
+    S = dwf.pseudofermion_action(pt, Ut, op, tol=1e-13)
+    S.backward()
+    S_ref, X_ref, _, G_ref, _ = oracle_lib.pf_force(dims, Ls, M5, MASS, BC, U, phi, tol=1e-13)
+    assert abs(S.item() - S_ref) < 1e-11 * S_ref
+    assert rel(host(pt.grad), 2.0 * X_ref) < 1e-8
+    assert rel(host(Ut.grad), G_ref) < 1e-8
+
+
 # ---------------------------------------------------------------- errors are reported, not raised on the GPU
 
 
