@@ -4,9 +4,9 @@
 
 namespace gdwf {
 
-template <bool DAG, bool C12, int LSC, bool EPI>
+template <bool DAG, bool C12, int LSC, int EK>
 static cudaError_t launch_one(const DhopArgs& a, int threads, int blocks, size_t smem, cudaStream_t stream) {
-  auto kern = dhop_kernel<DWF_PREC, DAG, C12, LSC, EPI>;
+  auto kern = dhop_kernel<DWF_PREC, DAG, C12, LSC, EK>;
   if (smem > 48 * 1024) {
     static size_t configured = 0;  // per instantiation
     if (smem > configured) {
@@ -43,20 +43,25 @@ static cudaError_t launch_ls(const DhopArgs& a, bool dag, bool c12, int threads,
                  : launch_tma<false, false, LSC>(a, threads, blocks, smem, stream);
     }
   }
-  // A launch without pre- or post-operation runs the instantiation compiled without the epilogue
-  // code (fewer live registers); FP64 always runs the general one.
-  const bool epi = DWF_PREC == P64 || a.pre != PRE_NONE || a.post != POST_NONE;
-  if (epi) {
-    if (dag) return c12 ? launch_one<true, true, LSC, true>(a, threads, blocks, smem, stream)
-                        : launch_one<true, false, LSC, true>(a, threads, blocks, smem, stream);
-    return c12 ? launch_one<false, true, LSC, true>(a, threads, blocks, smem, stream)
-               : launch_one<false, false, LSC, true>(a, threads, blocks, smem, stream);
-  }
-  if constexpr (DWF_PREC != P64) {
-    if (dag) return c12 ? launch_one<true, true, LSC, false>(a, threads, blocks, smem, stream)
-                        : launch_one<true, false, LSC, false>(a, threads, blocks, smem, stream);
-    return c12 ? launch_one<false, true, LSC, false>(a, threads, blocks, smem, stream)
-               : launch_one<false, false, LSC, false>(a, threads, blocks, smem, stream);
+  if constexpr (DWF_PREC == P64) {
+    if (dag) return c12 ? launch_one<true, true, LSC, EPI_BOTH>(a, threads, blocks, smem, stream)
+                        : launch_one<true, false, LSC, EPI_BOTH>(a, threads, blocks, smem, stream);
+    return c12 ? launch_one<false, true, LSC, EPI_BOTH>(a, threads, blocks, smem, stream)
+               : launch_one<false, false, LSC, EPI_BOTH>(a, threads, blocks, smem, stream);
+  } else {
+    // the instantiation with exactly the epilogue parts this launch uses; links format at run time
+    const int ek = (a.pre != PRE_NONE ? EPI_PRE : 0) | (a.post != POST_NONE ? EPI_POST : 0);
+#define DWF_EK(K)                                                                      \
+  case K:                                                                              \
+    return dag ? launch_one<true, false, LSC, K>(a, threads, blocks, smem, stream)     \
+               : launch_one<false, false, LSC, K>(a, threads, blocks, smem, stream);
+    switch (ek) {
+      DWF_EK(EPI_NONE)
+      DWF_EK(EPI_PRE)
+      DWF_EK(EPI_POST)
+      DWF_EK(EPI_BOTH)
+    }
+#undef DWF_EK
   }
   return cudaErrorInvalidValue;
 }

@@ -46,6 +46,7 @@ struct DhopArgs {
   int nsg;            // threads per site (slice pairs, or slices in FP64)
   int sites_per_cta;  // whole sites per CTA
   int pre, post;
+  int c12;            // links stored as two rows (packed kernels read this at run time)
   double alpha, beta;
   double d5;       // 5 - M5
   double mass;     // m
@@ -578,6 +579,22 @@ __device__ __forceinline__ void load_slice(const char* blk, int s, int Lsh, type
   }
 }
 
+// Packed precisions: reals r0 .. r0 + 11 (r0 = 0: the upper, P+ spins; 12: the lower) of slice s,
+// widened to FP32.
+template <int P>
+__device__ __forceinline__ void load_slice_half(const char* blk, int s, int Lsh, int r0, float* v) {
+  constexpr int VEC = Store<P>::VEC, RV = Store<P>::RV;
+  const int l = s & 1;
+  const char* b = blk + (size_t)(s >> 1) * 16;
+#pragma unroll
+  for (int k = 0; k < 12 / RV; ++k) {
+    float t[VEC];
+    ld16<P>(b + (size_t)(r0 / RV + k) * Lsh * 16, t);
+#pragma unroll
+    for (int j = 0; j < RV; ++j) v[RV * k + j] = t[2 * j + l];
+  }
+}
+
 // (Mooee aux)_s or (Mooee^+ aux)_s for one slice s < Ls (zero for the pad slice): the upper (P+)
 // reals couple to s-1 and the lower (P-) reals to s+1, with +m replacing -1 on the wrap-around;
 // the adjoint swaps them. GLOBAL = false reads a block staged in shared memory.
@@ -634,12 +651,18 @@ __device__ __forceinline__ void mooee_inv_line(R* v, int Ls, bool forward_form, 
 
 // ---------------------------------------------------------------- kernel bodies
 
-// FP32 / FP16 / BF16: one thread per (site, slice pair), packed two-wide arithmetic. EPI = false
-// compiles the kernel without the epilogue (pre = post = none).
-template <int P, bool DAG, bool C12, int LSC, bool EPI>
+// Epilogue kinds compiled into a packed kernel: bit 0 the pre-operation (aux, Mooee aux, Mooee^+
+// aux), bit 1 the post-operation (Mooee^-1, (Mooee^+)^-1). A launch runs the instantiation with
+// exactly the parts it uses, so plain hops and single-epilogue hops keep fewer live registers.
+enum EpiKind : int { EPI_NONE = 0, EPI_PRE = 1, EPI_POST = 2, EPI_BOTH = 3 };
+
+// FP32 / FP16 / BF16: one thread per (site, slice pair), packed two-wide arithmetic. The storage
+// of the links (18 or 12 reals, a.c12) only matters while they are staged, so it is a run-time
+// flag here.
+template <int P, bool DAG, int LSC, int EK>
 __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
   using T = typename Store<P>::T;
-  constexpr int LB = link_bytes(sizeof(T), C12);
+  const int LB = link_bytes(sizeof(T), a.c12 != 0);
   constexpr int SF = DAG ? +1 : -1;  // forward projector (1 + SF gamma)
   constexpr int SB = -SF;            // backward projector
   constexpr int LSHC = LSC > 0 ? ls_half(LSC) : 0;
@@ -665,7 +688,7 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
   // The eight links of each site, staged once per CTA as FP32: thread q of a site fetches the
   // links of hops q, q + Lsh, ... (hop h = 2 mu + backward), so every link is requested from
   // memory once instead of once per slice pair; the hops then read them from shared memory.
-  constexpr int LSS = dhop_link_site_bytes(P, C12);
+  constexpr int LSS = dhop_link_site_bytes(P, false);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   char* lsm = reinterpret_cast<char*>(smem_raw) + (size_t)site_local * LSS;  // [hop 8][80 bytes]
   const char* Uo = static_cast<const char*>(a.Uout);
@@ -681,7 +704,10 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
     for (int h = q; h < 8; h += Lsh) {
       const int mu = h >> 1;
       const char* src = (h & 1) == 0 ? Uo + ((size_t)site * 4 + mu) * LB : Ui + ((size_t)nb[h] * 4 + mu) * LB;
-      stage_link_f32<P, C12>(lsm + h * DHOP_LINK_F32_BYTES, src);
+      if (a.c12)
+        stage_link_f32<P, true>(lsm + h * DHOP_LINK_F32_BYTES, src);
+      else
+        stage_link_f32<P, false>(lsm + h * DHOP_LINK_F32_BYTES, src);
     }
   }
   __syncthreads();
@@ -728,7 +754,7 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
 
   // ------------------------------------------------------------ epilogue
   char* outb = static_cast<char*>(a.out) + (size_t)site * site_bytes;
-  if (EPI && active && a.pre != PRE_NONE) {
+  if ((EK & EPI_PRE) && active && a.pre != PRE_NONE) {
     const char* auxb = static_cast<const char*>(a.aux) + (size_t)site * site_bytes;
     const float2 B = f2((float)a.beta);
     if (a.pre == PRE_AUX) {
@@ -737,20 +763,45 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
 #pragma unroll
       for (int r = 0; r < 24; ++r) acc[r] = ffma2(B, o[r], acc[r]);
     } else {
-      float o0[24], o1[24];
-      if (a.pre == PRE_MOOEE) {
-        mooee_slice<P, false>(auxb, 2 * q, Ls, Lsh, a.d5, a.mass, o0);
-        mooee_slice<P, false>(auxb, 2 * q + 1, Ls, Lsh, a.d5, a.mass, o1);
-      } else {
-        mooee_slice<P, true>(auxb, 2 * q, Ls, Lsh, a.d5, a.mass, o0);
-        mooee_slice<P, true>(auxb, 2 * q + 1, Ls, Lsh, a.d5, a.mass, o1);
-      }
+      // beta (Mooee aux)_s = beta ((5 - M5) aux_s + c_up aux_{s_up}[upper] + c_lo aux_{s_lo}[lower]):
+      // the pair's own slices once, then only the 12-real half of each coupled neighbour slice.
+      const bool dag5 = a.pre == PRE_MOOEE_DAG;
+      const float beta = (float)a.beta, mass = (float)a.mass;
+      float2 own[24];
+      load_pair<P, LSHC>(auxb, q, Lsh, own);
+      const float2 BD = f2(beta * (float)a.d5);
 #pragma unroll
-      for (int r = 0; r < 24; ++r) acc[r] = ffma2(B, make_float2(o0[r], o1[r]), acc[r]);
+      for (int r = 0; r < 24; ++r) acc[r] = ffma2(BD, own[r], acc[r]);
+#pragma unroll
+      for (int l = 0; l < 2; ++l) {
+        const int s = 2 * q + l;
+        if (s >= Ls) continue;  // the zero pad slice
+        const int sm = s > 0 ? s - 1 : Ls - 1, sp = s < Ls - 1 ? s + 1 : 0;
+        const float cm = s > 0 ? -1.f : mass, cp = s < Ls - 1 ? -1.f : mass;
+        const int s_up = dag5 ? sp : sm, s_lo = dag5 ? sm : sp;
+        const float c_up = beta * (dag5 ? cp : cm), c_lo = beta * (dag5 ? cm : cp);
+        float x[12];
+        load_slice_half<P>(auxb, s_up, Lsh, 0, x);
+#pragma unroll
+        for (int r = 0; r < 12; ++r) {
+          if (l == 0)
+            acc[r].x = fmaf(c_up, x[r], acc[r].x);
+          else
+            acc[r].y = fmaf(c_up, x[r], acc[r].y);
+        }
+        load_slice_half<P>(auxb, s_lo, Lsh, 12, x);
+#pragma unroll
+        for (int r = 0; r < 12; ++r) {
+          if (l == 0)
+            acc[12 + r].x = fmaf(c_lo, x[r], acc[12 + r].x);
+          else
+            acc[12 + r].y = fmaf(c_lo, x[r], acc[12 + r].y);
+        }
+      }
     }
   }
   const bool pad_lane = (Ls & 1) && q == Lsh - 1;  // slice 2q+1 is the zero pad
-  if (!EPI || a.post == POST_NONE) {
+  if (!(EK & EPI_POST) || a.post == POST_NONE) {
     if (active) {
       if (pad_lane) {
 #pragma unroll
@@ -762,7 +813,7 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
   }
   // Fifth-dimension inverse through shared memory (after the staged links): whole sites live in
   // this CTA.
-  float* sm = reinterpret_cast<float*>(smem_raw + dhop_link_smem_bytes(P, a.sites_per_cta, C12));
+  float* sm = reinterpret_cast<float*>(smem_raw + dhop_link_smem_bytes(P, a.sites_per_cta, false));
   if (active) {
     float* d0 = sm + ((size_t)site_local * Ls + 2 * q) * 24;
 #pragma unroll
@@ -931,12 +982,14 @@ inline int dhop_threads_per_site(int prec, int Ls) { return prec == P64 ? ls_pad
 #define DWF_LS_SPECIALISATIONS(M) M(8) M(12) M(16) M(24) M(32)
 inline bool dhop_ls_specialised(int Ls) { return Ls == 8 || Ls == 12 || Ls == 16 || Ls == 24 || Ls == 32; }
 
-template <int P, bool DAG, bool C12, int LSC, bool EPI>
+// P64: C12 selects the stored link format and EK is EPI_BOTH; packed precisions: C12 = false
+// (a.c12 at run time) and EK the epilogue kind.
+template <int P, bool DAG, bool C12, int LSC, int EK>
 __global__ void __launch_bounds__(DhopOccupancy<P>::THREADS, DhopOccupancy<P>::MIN_BLOCKS) dhop_kernel(const __grid_constant__ DhopArgs a) {
   if constexpr (P == P64)
     dhop_body_lane64<DAG, C12, LSC>(a);
   else
-    dhop_body_pair<P, DAG, C12, LSC, EPI>(a);
+    dhop_body_pair<P, DAG, LSC, EK>(a);
 }
 
 // Host-side launcher, instantiated once per storage precision in its own translation unit.
