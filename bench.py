@@ -378,6 +378,78 @@ def run_pf_force(dwf, torch, spec):
     return out
 
 
+def run_sweep32(dwf, torch, steps=20, warmup=3):
+    """Roofline sweep of DhopEO + DhopOE at 32^4 x 16 (exp(0.5 i H) links, m = 0.005): FP32, FP16,
+    BF16 and FP64 storage. One operand set: a 32^4 x 16 half field (805 MB in FP32) is larger than
+    L2, so no rotation is needed. Fields are drawn on the device by the seeded generators."""
+    spec = synth.WORKLOADS["dwf_32x32x32x32_ls16_exp0.5"]
+    dims, Ls = spec["dims"], spec["Ls"]
+    n5 = int(np.prod(dims)) // 2 * Ls
+    hbm_peak, _ = peaks()
+    dev = torch.device("cuda")
+    U = synth.random_gauge_device(dims, 1000 * spec["case"], spec["eps"], dev)
+    psi = synth.random_spinor_device(dims, Ls, 1000 * spec["case"] + 1, dev)
+    op = dwf.GridDWF(dims, Ls, spec["M5"], spec["mass"], bc=BC)
+    op.set_gauge(U)
+    del U
+    out = {"workload": "dwf_32x32x32x32_ls16_exp0.5", "steps": steps, "l2": "one set, half field > L2"}
+    stream = torch.cuda.current_stream()
+    for name, prec, rb in (("f32", dwf.FP32, 4), ("f16", dwf.FP16, 2), ("bf16", dwf.BF16, 2), ("f64", dwf.FP64, 8)):
+        src = op.pack(psi, prec, dwf.FULL)
+        dst = op.field(prec, dwf.FULL, zero=True)
+        half = op.half_reals
+        n = steps if name != "f64" else max(2, steps // 10)
+        for _ in range(warmup):
+            op.dhop(src[half:], dwf.EVEN, out=dst[:half])
+            op.dhop(src[:half], dwf.ODD, out=dst[half:])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            op.dhop(src[half:], dwf.EVEN, out=dst[:half])
+            op.dhop(src[:half], dwf.ODD, out=dst[half:])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        per_launch = e0.elapsed_time(e1) / 1e3 / (2 * n)
+        gbs = algorithmic_bytes_per_site(rb, Ls) * n5 / per_launch / 1e9
+        rec = {"us_per_launch": round(per_launch * 1e6, 2), "gflops": round(FLOPS_PER_SITE * n5 / per_launch / 1e9, 1),
+               "algorithmic_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4)}
+        if name == "f64":
+            rec["alu_frac"] = round(rec["gflops"] / (FP64_ALU_TFLOPS * 1e3), 4)
+        out[name] = rec
+        del src, dst
+    op.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_cg32(dwf, torch):
+    """Mixed-precision vs FP64 CG at 32^4 x 16, m = 0.005, exp(0.5 i H) links, one Gaussian source,
+    to a 1e-10 true residual (optional: the FP64 solve takes tens of seconds)."""
+    spec = synth.WORKLOADS["dwf_32x32x32x32_ls16_exp0.5"]
+    dims, Ls = spec["dims"], spec["Ls"]
+    dev = torch.device("cuda")
+    op = dwf.GridDWF(dims, Ls, spec["M5"], spec["mass"], bc=BC)
+    op.set_gauge(synth.random_gauge_device(dims, 1000 * spec["case"], spec["eps"], dev))
+    b = op.pack(synth.random_spinor_device(dims, Ls, 1000 * spec["case"] + 2, dev), dwf.FP64, dwf.FULL)
+    out = {"workload": "dwf_32x32x32x32_ls16_exp0.5", "tol": 1e-10}
+    x64 = None
+    for name, mode in (("mixed_fp32", dwf.CG_MIXED_FP32), ("mixed_fp16", dwf.CG_MIXED_FP16), ("fp64", dwf.CG_FP64)):
+        x, st = op.cg(b, tol=1e-10, maxiter=20000, mode=mode, raise_on_fail=False)
+        out[name] = {"seconds": round(st.seconds, 3), "iterations": st.iterations,
+                     "reliable_updates": st.reliable_updates, "true_residual": st.true_residual,
+                     "converged": st.converged}
+        if name == "mixed_fp32":
+            x64 = x.clone()
+        elif x64 is not None:
+            out[name]["rel_diff_vs_mixed_fp32_solution"] = float(torch.linalg.vector_norm(x - x64) /
+                                                                 torch.linalg.vector_norm(x64))
+    out["speedup_mixed_fp32_vs_fp64"] = round(out["fp64"]["seconds"] / out["mixed_fp32"]["seconds"], 2)
+    out["speedup_mixed_fp16_vs_fp64"] = round(out["fp64"]["seconds"] / out["mixed_fp16"]["seconds"], 2)
+    op.close()
+    return out
+
+
 def cpu_baseline_sample(spec, target_seconds=10.0):
     """The FP64 oracle as it stands, DhopEO + DhopOE on the full lattice, on all host cores."""
     import oracle
@@ -493,6 +565,10 @@ def gpu_arm(args):
     }
     if not args.no_cg and rank == 0:
         line["cg"] = run_cg(dwf, torch, synth.WORKLOADS[CG_WORKLOAD])
+    if not args.no_sweep and rank == 0:
+        line["sweep_32x32x32x32_ls16"] = run_sweep32(dwf, torch)
+    if args.cg32 and rank == 0:
+        line["cg_32x32x32x32_ls16"] = run_cg32(dwf, torch)
     if not args.no_force and rank == 0:
         line["force"] = run_force(dwf, torch, synth.WORKLOADS["dwf_16x16x16x16_ls16_haar"])
         line["pf_force"] = run_pf_force(dwf, torch, spec)
@@ -553,6 +629,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cg", action="store_true", help="skip the CG time-to-solution comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the 32^4 x 16 Dhop roofline sweep")
+    ap.add_argument("--cg32", action="store_true", help="also run the 32^4 x 16 mixed vs FP64 CG (slow)")
     ap.add_argument("--no-force", action="store_true", help="skip the action/force and pseudofermion force timing")
     args = ap.parse_args(argv)
     if args.warmup < 3:

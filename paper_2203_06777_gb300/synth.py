@@ -34,6 +34,8 @@ __all__ = [
     "random_spinor",
     "random_su3_transform",
     "random_su3_algebra",
+    "random_spinor_device",
+    "random_gauge_device",
     "unit_gauge",
     "WORKLOADS",
 ]
@@ -107,6 +109,33 @@ def random_su3_algebra(shape, seed: int) -> np.ndarray:
     x = 0.5 * (a - np.conj(np.swapaxes(a, -1, -2)))
     tr = np.trace(x, axis1=-2, axis2=-1)
     return x - (tr / 3.0)[..., None, None] * np.eye(3)
+
+
+def random_spinor_device(dims, Ls: int, seed: int, device):
+    """Same distribution as random_spinor, drawn on a CUDA device by torch's seeded generator
+    (a different stream of numbers than the NumPy one; for timing runs on large lattices)."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    shape = _shape4(dims) + (int(Ls), 4, 3, 2)
+    x = torch.randn(shape, generator=g, device=device, dtype=torch.float64) * np.sqrt(0.5)
+    return torch.view_as_complex(x)
+
+
+def random_gauge_device(dims, seed: int, eps: float, device):
+    """exp(i eps H) links as in random_gauge, drawn on a CUDA device by torch's seeded generator;
+    H the traceless Hermitian part of a complex Gaussian matrix, the exponential by torch."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    shape = _shape4(dims) + (4, 3, 3, 2)
+    a = torch.view_as_complex(torch.randn(shape, generator=g, device=device, dtype=torch.float64) * np.sqrt(0.5))
+    h = 0.5 * (a + a.conj().transpose(-1, -2))
+    tr = torch.diagonal(h, dim1=-2, dim2=-1).sum(-1).real
+    h = h - (tr / 3.0)[..., None, None] * torch.eye(3, dtype=h.dtype, device=device)
+    return torch.linalg.matrix_exp(1j * eps * h).contiguous()
 
 
 # The benchmark and parity workloads. Each names its lattice, fifth-dimension extent,
