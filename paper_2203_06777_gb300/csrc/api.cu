@@ -163,9 +163,10 @@ int dhop_half(grid_dwf_t* h, int prec, const void* in, void* out, int out_parity
   a.nsg = dhop_threads_per_site(prec, h->Ls);
   a.sites_per_cta = 128 / a.nsg;
   if (a.sites_per_cta < 1) a.sites_per_cta = 1;
+  if (a.sites_per_cta > h->g.N4h) a.sites_per_cta = h->g.N4h;  // tiny lattices: one full CTA
   a.pre = pre;
   a.post = post;
-  a.c12 = h->c12 ? 1 : 0;
+  a.site_base = 0;
   a.alpha = alpha;
   a.beta = beta;
   a.d5 = h->d5;
@@ -180,7 +181,7 @@ int dhop_half(grid_dwf_t* h, int prec, const void* in, void* out, int out_parity
                 (post != POST_NONE ? (size_t)a.sites_per_cta * h->Ls * 24 * rbytes : 0);
   // Staged (bulk-copy) kernel for the bandwidth-bound precisions when a row segment fits.
   a.seg = 0;
-  if (h->staged && prec != GRID_DWF_FP64 && dhop_ls_specialised(h->Ls)) {
+  if (h->staged && prec != GRID_DWF_FP64 && dhop_tma_ls(h->Ls)) {
     const size_t post_site = post != POST_NONE ? (size_t)h->Ls * 24 * rbytes : 0;
     a.seg = tma_choose_seg(h->g.Lxh, h->Ls, prec_bytes(prec), h->c12, post_site);
   }

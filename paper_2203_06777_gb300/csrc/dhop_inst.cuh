@@ -15,7 +15,19 @@ static cudaError_t launch_one(const DhopArgs& a, int threads, int blocks, size_t
       configured = smem;
     }
   }
-  kern<<<blocks, threads, smem, stream>>>(a);
+  if constexpr (DWF_PREC == P64) {
+    kern<<<blocks, threads, smem, stream>>>(a);
+  } else {
+    // full CTAs only (the packed kernel has no tail handling); a ragged end gets one more CTA
+    // flush with the end of the lattice, launched after the first so no two writes overlap in time
+    const int full = a.g.N4h / a.sites_per_cta;
+    if (full > 0) kern<<<full, threads, smem, stream>>>(a);
+    if (full * a.sites_per_cta != a.g.N4h) {
+      DhopArgs t = a;
+      t.site_base = a.g.N4h - a.sites_per_cta;
+      kern<<<1, threads, smem, stream>>>(t);
+    }
+  }
   return cudaGetLastError();
 }
 
@@ -35,7 +47,7 @@ static cudaError_t launch_tma(const DhopArgs& a, int threads, int blocks, size_t
 template <int LSC>
 static cudaError_t launch_ls(const DhopArgs& a, bool dag, bool c12, int threads, int blocks, size_t smem,
                              cudaStream_t stream) {
-  if constexpr (LSC > 0 && DWF_PREC != P64) {
+  if constexpr ((LSC == 8 || LSC == 16) && DWF_PREC != P64) {
     if (a.seg > 0) {
       if (dag) return c12 ? launch_tma<true, true, LSC>(a, threads, blocks, smem, stream)
                           : launch_tma<true, false, LSC>(a, threads, blocks, smem, stream);
@@ -49,11 +61,13 @@ static cudaError_t launch_ls(const DhopArgs& a, bool dag, bool c12, int threads,
     return c12 ? launch_one<false, true, LSC, EPI_BOTH>(a, threads, blocks, smem, stream)
                : launch_one<false, false, LSC, EPI_BOTH>(a, threads, blocks, smem, stream);
   } else {
-    // the instantiation with exactly the epilogue parts this launch uses; links format at run time
+    // the instantiation with exactly the epilogue parts this launch uses
     const int ek = (a.pre != PRE_NONE ? EPI_PRE : 0) | (a.post != POST_NONE ? EPI_POST : 0);
-#define DWF_EK(K)                                                                      \
-  case K:                                                                              \
-    return dag ? launch_one<true, false, LSC, K>(a, threads, blocks, smem, stream)     \
+#define DWF_EK(K)                                                                             \
+  case K:                                                                                     \
+    if (dag) return c12 ? launch_one<true, true, LSC, K>(a, threads, blocks, smem, stream)    \
+                        : launch_one<true, false, LSC, K>(a, threads, blocks, smem, stream);  \
+    return c12 ? launch_one<false, true, LSC, K>(a, threads, blocks, smem, stream)            \
                : launch_one<false, false, LSC, K>(a, threads, blocks, smem, stream);
     switch (ek) {
       DWF_EK(EPI_NONE)

@@ -46,7 +46,7 @@ struct DhopArgs {
   int nsg;            // threads per site (slice pairs, or slices in FP64)
   int sites_per_cta;  // whole sites per CTA
   int pre, post;
-  int c12;            // links stored as two rows (packed kernels read this at run time)
+  int site_base;      // packed kernels: first site of block 0 (every CTA of a launch is full)
   double alpha, beta;
   double d5;       // 5 - M5
   double mass;     // m
@@ -656,13 +656,11 @@ __device__ __forceinline__ void mooee_inv_line(R* v, int Ls, bool forward_form, 
 // exactly the parts it uses, so plain hops and single-epilogue hops keep fewer live registers.
 enum EpiKind : int { EPI_NONE = 0, EPI_PRE = 1, EPI_POST = 2, EPI_BOTH = 3 };
 
-// FP32 / FP16 / BF16: one thread per (site, slice pair), packed two-wide arithmetic. The storage
-// of the links (18 or 12 reals, a.c12) only matters while they are staged, so it is a run-time
-// flag here.
-template <int P, bool DAG, int LSC, int EK>
+// FP32 / FP16 / BF16: one thread per (site, slice pair), packed two-wide arithmetic.
+template <int P, bool DAG, bool C12, int LSC, int EK>
 __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
   using T = typename Store<P>::T;
-  const int LB = link_bytes(sizeof(T), a.c12 != 0);
+  constexpr int LB = link_bytes(sizeof(T), C12);
   constexpr int SF = DAG ? +1 : -1;  // forward projector (1 + SF gamma)
   constexpr int SB = -SF;            // backward projector
   constexpr int LSHC = LSC > 0 ? ls_half(LSC) : 0;
@@ -671,13 +669,12 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
   const int tid = threadIdx.x;
   const int site_local = tid / Lsh;
   const int q = tid - site_local * Lsh;
-  // Every launch has exactly threads-per-site x sites_per_cta threads (dhop_half), so only the
-  // last CTA can hold threads past the end of the lattice. They run the same straight-line code
-  // on the last site (a valid address) and store nothing: a guard around the hop loop instead
-  // measured 5-7% slower.
-  const int site_raw = blockIdx.x * a.sites_per_cta + site_local;
-  const bool active = site_raw < a.g.N4h;
-  const int site = active ? site_raw : a.g.N4h - 1;
+  // Every CTA of a launch is full: the launcher covers a ragged end of the lattice with a second,
+  // one-CTA launch whose site_base places it flush with the end (it rewrites a few sites with the
+  // same values). The kernel then has no tail handling at all: a per-thread guard around the hop
+  // loop, or a clamped site index, measured 5-10% slower.
+  const int site = a.site_base + (int)blockIdx.x * a.sites_per_cta + site_local;
+  constexpr bool active = true;
   const size_t site_bytes = (size_t)Lsh * 2 * 24 * sizeof(T);
   const float alpha = (float)a.alpha;
 
@@ -704,10 +701,7 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
     for (int h = q; h < 8; h += Lsh) {
       const int mu = h >> 1;
       const char* src = (h & 1) == 0 ? Uo + ((size_t)site * 4 + mu) * LB : Ui + ((size_t)nb[h] * 4 + mu) * LB;
-      if (a.c12)
-        stage_link_f32<P, true>(lsm + h * DHOP_LINK_F32_BYTES, src);
-      else
-        stage_link_f32<P, false>(lsm + h * DHOP_LINK_F32_BYTES, src);
+      stage_link_f32<P, C12>(lsm + h * DHOP_LINK_F32_BYTES, src);
     }
   }
   __syncthreads();
@@ -824,8 +818,7 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
     }
   }
   __syncthreads();
-  const int first_site = blockIdx.x * a.sites_per_cta;
-  const int nsites = min(a.sites_per_cta, a.g.N4h - first_site);
+  const int nsites = a.sites_per_cta;
   for (int task = tid; task < nsites * 24; task += blockDim.x) {
     const int sl = task / 24;
     const int r = task - sl * 24;
@@ -979,17 +972,18 @@ struct DhopOccupancy {
 inline int dhop_threads_per_site(int prec, int Ls) { return prec == P64 ? ls_padded(Ls) : ls_half(Ls); }
 
 // Ls values with a compile-time specialisation; any other Ls runs the generic kernel (LSC = 0).
-#define DWF_LS_SPECIALISATIONS(M) M(8) M(12) M(16) M(24) M(32)
-inline bool dhop_ls_specialised(int Ls) { return Ls == 8 || Ls == 12 || Ls == 16 || Ls == 24 || Ls == 32; }
+#define DWF_LS_SPECIALISATIONS(M) M(8) M(12) M(16)
+inline bool dhop_ls_specialised(int Ls) { return Ls == 8 || Ls == 12 || Ls == 16; }
+// Ls values of the opt-in bulk-copy staged kernel (dhop_tma.cuh).
+inline bool dhop_tma_ls(int Ls) { return Ls == 8 || Ls == 16; }
 
-// P64: C12 selects the stored link format and EK is EPI_BOTH; packed precisions: C12 = false
-// (a.c12 at run time) and EK the epilogue kind.
+// C12 selects the stored link format; EK the epilogue kind (EPI_BOTH for FP64).
 template <int P, bool DAG, bool C12, int LSC, int EK>
 __global__ void __launch_bounds__(DhopOccupancy<P>::THREADS, DhopOccupancy<P>::MIN_BLOCKS) dhop_kernel(const __grid_constant__ DhopArgs a) {
   if constexpr (P == P64)
     dhop_body_lane64<DAG, C12, LSC>(a);
   else
-    dhop_body_pair<P, DAG, LSC, EK>(a);
+    dhop_body_pair<P, DAG, C12, LSC, EK>(a);
 }
 
 // Host-side launcher, instantiated once per storage precision in its own translation unit.
