@@ -121,7 +121,7 @@ def test_dhop_parity(dwf, oracle_lib, dims, Ls, eps, prec):
 
 
 @pytest.mark.parametrize("prec", [2, 3])
-@pytest.mark.parametrize("dims,Ls", [((4, 4, 4, 4), 8), ((2, 4, 6, 4), 3), ((4, 4, 2, 2), 16)])
+@pytest.mark.parametrize("dims,Ls", [(d, ls) for d, ls, _ in DHOP_CASES] + [((4, 4, 2, 2), 16)])
 def test_dhop_low_precision_storage(dwf, oracle_lib, prec, dims, Ls):
     op, U = make(dwf, dims, Ls, 21, eps=0.3)
     psi = synth.random_spinor(dims, Ls, seed=22)
@@ -486,22 +486,44 @@ def test_full_size_dhop_16x16x16x16_ls16(dwf, oracle_lib, prec):
     assert rel(got, ref) < TOL[prec], rel(got, ref)
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_full_size_dhop_32x32x32x32_ls16_sampled(dwf, oracle_lib, prec):
+@pytest.fixture(scope="module")
+def fields_32():
     w = _workload("dwf_32x32x32x32_ls16_exp0.5")
+    U = synth.random_gauge(w["dims"], seed=1000 * w["case"], eps=w["eps"])
+    psi = synth.random_spinor(w["dims"], w["Ls"], seed=1000 * w["case"] + 1)
+    return w, U, psi
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+def test_full_size_dhop_32x32x32x32_ls16_sampled(dwf, oracle_lib, fields_32, prec):
+    w, U, psi = fields_32
     dims, Ls = w["dims"], w["Ls"]
-    U = synth.random_gauge(dims, seed=1000 * w["case"], eps=w["eps"])
-    psi = synth.random_spinor(dims, Ls, seed=1000 * w["case"] + 1)
     op = dwf.GridDWF(dims, Ls, w["M5"], w["mass"], bc=BC)
     op.set_gauge(dev(U))
     f = op.pack(dev(psi), prec, dwf.FULL)
     got = host(op.unpack(op.dhop(f, dwf.FULL))).reshape(-1, Ls, 4, 3)
+    op.close()
     rng = np.random.default_rng(77)
     sites = rng.choice(int(np.prod(dims)), size=256, replace=False)
     lx, ly, lz, lt = dims
     # include the lattice corners, where every hop wraps around
     sites = np.concatenate([sites, [0, lx - 1, lx * ly * lz * lt - 1]])
-    ref = oracle_lib.dhop_sites(dims, Ls, BC, round_spinor(U, prec), round_spinor(psi, prec), sites)
+    # the oracle reads only the sampled sites and their 8 neighbours: round just those
+    V = int(np.prod(dims))
+    need = set(int(x) for x in sites)
+    for x in sites:
+        c = [int(x) % lx, int(x) // lx % ly, int(x) // (lx * ly) % lz, int(x) // (lx * ly * lz)]
+        for mu in range(4):
+            for d in (1, -1):
+                cn = list(c)
+                cn[mu] = (cn[mu] + d) % dims[mu]
+                need.add(cn[0] + lx * (cn[1] + ly * (cn[2] + lz * cn[3])))
+    idx = np.array(sorted(need))
+    psi_r = psi.reshape(V, Ls, 4, 3).copy()
+    U_r = U.reshape(V, 4, 3, 3).copy()
+    psi_r[idx] = round_spinor(psi_r[idx], prec)
+    U_r[idx] = round_spinor(U_r[idx], prec)
+    ref = oracle_lib.dhop_sites(dims, Ls, BC, U_r.reshape(U.shape), psi_r.reshape(psi.shape), sites)
     assert rel(got[sites], ref) < TOL[prec]
 
 
