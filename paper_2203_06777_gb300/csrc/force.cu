@@ -13,176 +13,238 @@
 // Because (1 -+ gamma_mu)/2 is a rank-2 projector, each spin sum is the sum over the two spins
 // of the projected half spinors: sum_spin a (x) [(1 - gamma) b]^+ = sum_{h=0,1} (P a)_h (x) (P b)_h^*.
 //
-// Thread mapping: one thread per link (x, mu), looping over the slices. FP32 fields: each slice
-// pair is projected and multiplied in packed FP32x2 arithmetic and summed in FP32 over blocks of
-// at most 8 pairs, each block then added into FP64 accumulators (GB300's FP64 pipe is 1/64 of
-// FP32, so per-pair FP64 adds would dominate the kernel); FP64 fields use FP64 throughout. The link algebra (U B1, B2 U^+, the traceless anti-Hermitian projection) is FP64,
-// and F and G are written in the canonical FP64 layout [t][z][y][x][mu][3][3].
+// Thread mapping, as in the hopping kernel: one thread per (4D site, slice pair) for FP32 fields
+// and per (4D site, slice) for FP64, whole sites per CTA, one parity per grid row. For each mu the
+// threads form their slices' contributions to B1 and B2 of the link U_mu(x) leaving their site
+// (the own spinors and the two x + mu neighbours, the same loads as one Dhop hop), the CTA sums
+// them over the site's slices through shared memory, and the link algebra is spread over the
+// CTA's threads (one 3x3 entry each). FP32 fields: the products are summed in FP32 over blocks of
+// at most 8 slice pairs and the block sums in FP64, and the link algebra (U B1, B2 U^+, the
+// traceless anti-Hermitian projection) runs in FP32 on those sums: GB300's FP64 pipe is 1/64 of
+// its FP32 pipe, and FP64 algebra made the kernel 5x slower for an answer whose error is set by
+// the FP32 fields and block sums anyway. FP64 fields use FP64 throughout. F and G are written
+// in the canonical FP64 layout [t][z][y][x][mu][3][3].
+#include <type_traits>
+
 #include "dhop_kernel.cuh"
 
 namespace gdwf {
 
+// Threads per site: slice pairs (FP32, at most 128 for Ls <= 256) or padded slices (FP64; above 128
+// slices each thread takes several); sites per CTA fill 128 threads.
+inline int force_threads_per_site(int prec, int Ls) {
+  const int n = prec == P64 ? ls_padded(Ls) : ls_half(Ls);
+  return n < 128 ? n : 128;
+}
+
+// Shared memory per site: partial sums of each slice thread (a stride of 37 values, odd, keeps
+// the threads' writes in distinct banks), the site's summed B1 and B2 (36), its link (18), Y (18)
+// and the output index and boundary phase.
+constexpr int FORCE_PART_STRIDE = 37;
+inline size_t force_smem_per_site(int prec, int nsg) {
+  const size_t v = prec == P64 ? sizeof(double) : sizeof(float);
+  return (size_t)nsg * FORCE_PART_STRIDE * v + (36 + 18 + 18) * v + 2 * sizeof(long);
+}
+
 template <int P, bool C12>
 __global__ void __launch_bounds__(128) k_force(const Geom g, const char* psi, const char* chi, const char* Ue,
-                                               const char* Uo, double* F, double* G, double coef) {
+                                               const char* Uo, double* F, double* G, double coef, int nsg, int spc) {
   using T = typename Store<P>::T;
   using R = typename Store<P>::R;
+  using A = typename std::conditional<P == P64, double, float>::type;  // partial sums and link algebra
   constexpr int LB = link_bytes(sizeof(T), C12);
-  const int Ls = g.Ls;
-  const int Lsh = ls_half(Ls);
+  constexpr int FLUSH = 8;  // FP32: slice pairs summed in FP32 before an FP64 sum across blocks
+  const int Lsh = ls_half(g.Ls);
   const size_t site_bytes = (size_t)Lsh * 2 * 24 * sizeof(T);
   const size_t half_bytes = (size_t)g.N4h * site_bytes;
-  const long link = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (link >= 8L * g.N4h) return;
-  const int mu = (int)(link & 3);
-  const long rest = link >> 2;
-  const int p = rest >= g.N4h ? 1 : 0;
-  const int i = (int)(rest - (long)p * g.N4h);
+  // both parities of a block of sites run next to each other, so their shared neighbours are
+  // still in L2 when the other parity reads them
+  const int p = blockIdx.x & 1;
+  const int first = (blockIdx.x >> 1) * spc;
+  const int tid = threadIdx.x;
+  const int site_local = tid / nsg;
+  const int t = tid - site_local * nsg;  // slice pair (FP32) or slice (FP64)
+  const int nsites = min(spc, g.N4h - first);
+  const bool active = site_local < nsites;
+  const int i = first + (active ? site_local : 0);
   int c[4];
   cb_coords(g, i, p, c);
-  int ph;
-  const int j = cb_neighbour(g, i, c, mu, true, ph);
   const char* psi_x = psi + p * half_bytes + (size_t)i * site_bytes;
   const char* chi_x = chi + p * half_bytes + (size_t)i * site_bytes;
-  const char* psi_f = psi + (1 - p) * half_bytes + (size_t)j * site_bytes;
-  const char* chi_f = chi + (1 - p) * half_bytes + (size_t)j * site_bytes;
 
-  double B1[18], B2[18];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  long* lex_sm = reinterpret_cast<long*>(smem_raw);                          // [spc]
+  int* ph_sm = reinterpret_cast<int*>(lex_sm + spc);                         // [spc] (pairs of ints: 8 bytes)
+  A* part = reinterpret_cast<A*>(smem_raw + (size_t)spc * 2 * sizeof(long));  // [spc][nsg][37]
+  A* bsum = part + (size_t)spc * nsg * FORCE_PART_STRIDE;                      // [spc][36]
+  A* usm = bsum + (size_t)spc * 36;                                            // [spc][18]
+  A* ysm = usm + (size_t)spc * 18;                                             // [spc][18]
+  if (active && t == 0) lex_sm[site_local] = c[0] + (long)g.L[0] * (c[1] + (long)g.L[1] * (c[2] + (long)g.L[2] * c[3]));
+
 #pragma unroll
-  for (int k = 0; k < 18; ++k) B1[k] = B2[k] = 0.0;
-  if constexpr (P == P64) {
+  for (int mu = 0; mu < 4; ++mu) {  // unrolled: direction-dependent indices stay compile-time
+    // ---- this thread's slices: B1 += psi(x+mu) (x) [(1 - gamma) chi(x)]^+, B2 += psi(x) (x) [(1 + gamma) chi(x+mu)]^+
+    if (active) {
+      int ph;
+      const int j = cb_neighbour(g, i, c, mu, true, ph);
+      if (t == 0) ph_sm[site_local] = ph;
+      const char* psi_f = psi + (1 - p) * half_bytes + (size_t)j * site_bytes;
+      const char* chi_f = chi + (1 - p) * half_bytes + (size_t)j * site_bytes;
+      A* dst = part + ((size_t)site_local * nsg + t) * FORCE_PART_STRIDE;
+      if constexpr (P == P64) {
+        double B[36];
 #pragma unroll
-    for (int term = 0; term < 2; ++term) {
-      double* B = term == 0 ? B1 : B2;
-      const char* fa = term == 0 ? psi_f : psi_x;
-      const char* fb = term == 0 ? chi_x : chi_f;
-      for (int s = 0; s < Ls; ++s) {
-        double v[24], ha[12], hb[12];
-        load_lane64<0>(fa, s, Lsh, v);
-        if (term == 0) project<-1>(mu, v, ha); else project<+1>(mu, v, ha);
-        load_lane64<0>(fb, s, Lsh, v);
-        if (term == 0) project<-1>(mu, v, hb); else project<+1>(mu, v, hb);
+        for (int k = 0; k < 36; ++k) B[k] = 0;
+        for (int sl5 = t; sl5 < 2 * Lsh; sl5 += nsg) {  // this thread's slices (one unless Ls > 128)
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-          for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {  // B[a][b] += ha[h][a] conj(hb[h][b])
-              const double xr = ha[(h * 3 + a) * 2], xi = ha[(h * 3 + a) * 2 + 1];
-              const double yr = hb[(h * 3 + b) * 2], yi = hb[(h * 3 + b) * 2 + 1];
-              B[(a * 3 + b) * 2] = fma(xr, yr, fma(xi, yi, B[(a * 3 + b) * 2]));
-              B[(a * 3 + b) * 2 + 1] = fma(xi, yr, fma(-xr, yi, B[(a * 3 + b) * 2 + 1]));
-            }
-      }
-    }
-  } else {
-    // Pad slices are zero in every field, so pairs are used whole. Each term is summed in
-    // FP32x2 (one lane per slice parity) over blocks of up to FLUSH pairs, and each block's two
-    // lanes are added into the FP64 accumulators: at most 2 FLUSH FP32 terms per rounding chain.
-    constexpr int FLUSH = 8;
-#pragma unroll
-    for (int term = 0; term < 2; ++term) {
-      double* B = term == 0 ? B1 : B2;
-      const char* fa = term == 0 ? psi_f : psi_x;
-      const char* fb = term == 0 ? chi_x : chi_f;
-      for (int q0 = 0; q0 < Lsh; q0 += FLUSH) {
-        float2 acc[18];
-#pragma unroll
-        for (int k = 0; k < 18; ++k) acc[k] = make_float2(0.f, 0.f);
-        const int q1 = min(q0 + FLUSH, Lsh);
-        for (int q = q0; q < q1; ++q) {
-          float2 v[24], ha[12], hb[12];
-          load_pair<P, 0>(fa, q, Lsh, v);
-          if (term == 0) project2<-1>(mu, v, ha); else project2<+1>(mu, v, ha);
-          load_pair<P, 0>(fb, q, Lsh, v);
-          if (term == 0) project2<-1>(mu, v, hb); else project2<+1>(mu, v, hb);
-#pragma unroll
-          for (int h = 0; h < 2; ++h)
+          for (int term = 0; term < 2; ++term) {
+            double v[24], ha[12], hb[12];
+            load_lane64<0>(term == 0 ? psi_f : psi_x, sl5, Lsh, v);
+            if (term == 0) project<-1>(mu, v, ha); else project<+1>(mu, v, ha);
+            load_lane64<0>(term == 0 ? chi_x : chi_f, sl5, Lsh, v);
+            if (term == 0) project<-1>(mu, v, hb); else project<+1>(mu, v, hb);
 #pragma unroll
             for (int a = 0; a < 3; ++a)
 #pragma unroll
-              for (int b = 0; b < 3; ++b) {  // acc[a][b] += ha[h][a] conj(hb[h][b])
+              for (int b = 0; b < 3; ++b) {  // sum_h ha[h][a] conj(hb[h][b])
+                double re = B[term * 18 + (a * 3 + b) * 2], im = B[term * 18 + (a * 3 + b) * 2 + 1];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                  const double xr = ha[(h * 3 + a) * 2], xi = ha[(h * 3 + a) * 2 + 1];
+                  const double yr = hb[(h * 3 + b) * 2], yi = hb[(h * 3 + b) * 2 + 1];
+                  re = fma(xr, yr, fma(xi, yi, re));
+                  im = fma(xi, yr, fma(-xr, yi, im));
+                }
+                B[term * 18 + (a * 3 + b) * 2] = re;
+                B[term * 18 + (a * 3 + b) * 2 + 1] = im;
+              }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 36; ++k) dst[k] = B[k];
+      } else {
+#pragma unroll
+        for (int term = 0; term < 2; ++term) {
+          float2 v[24], ha[12], hb[12];
+          load_pair<P, 0>(term == 0 ? psi_f : psi_x, t, Lsh, v);
+          if (term == 0) project2<-1>(mu, v, ha); else project2<+1>(mu, v, ha);
+          load_pair<P, 0>(term == 0 ? chi_x : chi_f, t, Lsh, v);
+          if (term == 0) project2<-1>(mu, v, hb); else project2<+1>(mu, v, hb);
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {  // both slices of the pair, then their sum
+              float2 re = make_float2(0.f, 0.f), im = make_float2(0.f, 0.f);
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
                 const float2 xr = ha[(h * 3 + a) * 2], xi = ha[(h * 3 + a) * 2 + 1];
                 const float2 yr = hb[(h * 3 + b) * 2], yi = hb[(h * 3 + b) * 2 + 1];
-                acc[(a * 3 + b) * 2] = ffma2(xr, yr, ffma2(xi, yi, acc[(a * 3 + b) * 2]));
-                acc[(a * 3 + b) * 2 + 1] =
-                    ffma2(xi, yr, ffma2(make_float2(-xr.x, -xr.y), yi, acc[(a * 3 + b) * 2 + 1]));
+                re = ffma2(xr, yr, ffma2(xi, yi, re));
+                im = ffma2(xi, yr, ffma2(make_float2(-xr.x, -xr.y), yi, im));
               }
+              dst[term * 18 + (a * 3 + b) * 2] = re.x + re.y;
+              dst[term * 18 + (a * 3 + b) * 2 + 1] = im.x + im.y;
+            }
         }
-#pragma unroll
-        for (int k = 0; k < 18; ++k) B[k] += (double)acc[k].x + (double)acc[k].y;
       }
     }
-  }
-
-  R ur[18];
-  load_link<P, C12>((p ? Uo : Ue) + ((size_t)i * 4 + mu) * LB, ur);
-  double u[18];
-#pragma unroll
-  for (int k = 0; k < 18; ++k) u[k] = (double)ur[k];
-  const double phd = coef * (double)ph;  // F and G are linear in the boundary phase and coef
-  const long lex = c[0] + (long)g.L[0] * (c[1] + (long)g.L[1] * (c[2] + (long)g.L[2] * c[3]));
-  double* Fo = F ? F + (lex * 4 + mu) * 18 : nullptr;
-  double* Go = G ? G + (lex * 4 + mu) * 18 : nullptr;
-  if (Go) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {  // G[a][b] = -phase (conj(B1[b][a]) + B2[a][b])
-        Go[(a * 3 + b) * 2] = -phd * (B1[(b * 3 + a) * 2] + B2[(a * 3 + b) * 2]);
-        Go[(a * 3 + b) * 2 + 1] = -phd * (-B1[(b * 3 + a) * 2 + 1] + B2[(a * 3 + b) * 2 + 1]);
-      }
-  }
-  if (Fo) {
-    double Y[18];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {  // Y = phase (-U B1 + B2 U^+)
-        double yr = 0, yi = 0;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const double ar = u[(a * 3 + k) * 2], ai = u[(a * 3 + k) * 2 + 1];
-          const double br = B1[(k * 3 + b) * 2], bi = B1[(k * 3 + b) * 2 + 1];
-          yr -= ar * br - ai * bi;
-          yi -= ar * bi + ai * br;
-          const double cr = B2[(a * 3 + k) * 2], ci = B2[(a * 3 + k) * 2 + 1];
-          const double dr = u[(b * 3 + k) * 2], di = -u[(b * 3 + k) * 2 + 1];  // (U^+)[k][b] = conj(U[b][k])
-          yr += cr * dr - ci * di;
-          yi += cr * di + ci * dr;
+    __syncthreads();
+    // ---- sum over the site's slices, one (site, entry) per task; and each site's link
+    for (int task = tid; task < nsites * 36; task += blockDim.x) {
+      const int sl = task / 36, e = task - sl * 36;
+      const A* src = part + (size_t)sl * nsg * FORCE_PART_STRIDE + e;
+      A total;
+      if constexpr (P == P64) {
+        total = 0;
+        for (int k = 0; k < nsg; ++k) total += src[(size_t)k * FORCE_PART_STRIDE];
+      } else if (nsg <= FLUSH) {  // one block: FP32 throughout
+        total = 0.f;
+        for (int k = 0; k < nsg; ++k) total += src[(size_t)k * FORCE_PART_STRIDE];
+      } else {  // blocks of FLUSH pairs summed in FP64
+        double acc = 0;
+        for (int k0 = 0; k0 < nsg; k0 += FLUSH) {
+          float blk = 0.f;
+          const int k1 = min(k0 + FLUSH, nsg);
+          for (int k = k0; k < k1; ++k) blk += src[(size_t)k * FORCE_PART_STRIDE];
+          acc += (double)blk;
         }
-        Y[(a * 3 + b) * 2] = phd * yr;
-        Y[(a * 3 + b) * 2 + 1] = phd * yi;
+        total = (A)acc;
       }
-    // F = -TA(Y): TA(Y)[a][b] = (Y[a][b] - conj(Y[b][a]))/2 - delta_ab tr(Y - Y^+)/6
-    const double trim = (Y[1] + Y[9] + Y[17]);  // Im tr Y; tr(Y - Y^+) = 2 i Im tr Y
+      bsum[(size_t)sl * 36 + e] = total;
+    }
+    for (int sl = tid; sl < nsites; sl += blockDim.x) {  // the link U_mu(x), third row rebuilt if stored as 12 reals
+      R ur[18];
+      load_link<P, C12>((p ? Uo : Ue) + ((size_t)(first + sl) * 4 + mu) * LB, ur);
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+      for (int k = 0; k < 18; ++k) usm[(size_t)sl * 18 + k] = (A)ur[k];
+    }
+    __syncthreads();
+    // ---- link algebra, one (site, a, b) entry per task:
+    //   G[a][b] = -phase (conj(B1[b][a]) + B2[a][b]),  Y = phase (-U B1 + B2 U^+)
+    for (int task = tid; task < nsites * 9; task += blockDim.x) {
+      const int sl = task / 9, ab = task - sl * 9, a = ab / 3, b = ab - a * 3;
+      const A phd = (A)(coef * (double)ph_sm[sl]);  // F and G are linear in the boundary phase and coef
+      const A* B1 = bsum + (size_t)sl * 36;
+      const A* B2 = B1 + 18;
+      const A* ur = usm + (size_t)sl * 18;
+      A yr = 0, yi = 0;
 #pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        double tr_ = 0.5 * (Y[(a * 3 + b) * 2] - Y[(b * 3 + a) * 2]);
-        double ti_ = 0.5 * (Y[(a * 3 + b) * 2 + 1] + Y[(b * 3 + a) * 2 + 1]);
-        if (a == b) ti_ -= trim / 3.0;
-        Fo[(a * 3 + b) * 2] = -tr_;
-        Fo[(a * 3 + b) * 2 + 1] = -ti_;
+      for (int k = 0; k < 3; ++k) {
+        const A ar = ur[(a * 3 + k) * 2], ai = ur[(a * 3 + k) * 2 + 1];
+        const A br = B1[(k * 3 + b) * 2], bi = B1[(k * 3 + b) * 2 + 1];
+        yr -= ar * br - ai * bi;
+        yi -= ar * bi + ai * br;
+        const A cr = B2[(a * 3 + k) * 2], ci = B2[(a * 3 + k) * 2 + 1];
+        const A dr = ur[(b * 3 + k) * 2], di = -ur[(b * 3 + k) * 2 + 1];  // (U^+)[k][b] = conj(U[b][k])
+        yr += cr * dr - ci * di;
+        yi += cr * di + ci * dr;
       }
+      ysm[(size_t)sl * 18 + ab * 2] = phd * yr;
+      ysm[(size_t)sl * 18 + ab * 2 + 1] = phd * yi;
+      if (G) {
+        double* Go = G + (lex_sm[sl] * 4 + mu) * 18;
+        Go[ab * 2] = (double)(-phd * (B1[(b * 3 + a) * 2] + B2[ab * 2]));
+        Go[ab * 2 + 1] = (double)(-phd * (-B1[(b * 3 + a) * 2 + 1] + B2[ab * 2 + 1]));
+      }
+    }
+    __syncthreads();
+    // ---- F = -TA(Y): TA(Y)[a][b] = (Y[a][b] - conj(Y[b][a]))/2 - delta_ab tr(Y - Y^+)/6
+    if (F) {
+      for (int task = tid; task < nsites * 9; task += blockDim.x) {
+        const int sl = task / 9, ab = task - sl * 9, a = ab / 3, b = ab - a * 3;
+        const A* Y = ysm + (size_t)sl * 18;
+        const A trim = Y[1] + Y[9] + Y[17];  // Im tr Y; tr(Y - Y^+) = 2 i Im tr Y
+        const A tr_ = (A)0.5 * (Y[(a * 3 + b) * 2] - Y[(b * 3 + a) * 2]);
+        A ti_ = (A)0.5 * (Y[(a * 3 + b) * 2 + 1] + Y[(b * 3 + a) * 2 + 1]);
+        if (a == b) ti_ -= trim / (A)3;
+        double* Fo = F + (lex_sm[sl] * 4 + mu) * 18;
+        Fo[ab * 2] = -(double)tr_;
+        Fo[ab * 2 + 1] = -(double)ti_;
+      }
+    }
+    __syncthreads();  // shared memory is reused by the next direction
   }
 }
 
 cudaError_t launch_force(int prec, bool c12, const Geom& g, const void* psi, const void* chi, const void* Ue,
                          const void* Uo, double* F, double* G, double coef, cudaStream_t st) {
-  const int threads = 128;
-  const long links = 8L * g.N4h;
-  const int blocks = (int)((links + threads - 1) / threads);
+  const int nsg = force_threads_per_site(prec, g.Ls);
+  const size_t per_site = force_smem_per_site(prec, nsg);
+  int spc = 128 / nsg;
+  if ((size_t)spc * per_site > 48 * 1024) spc = (int)(48 * 1024 / per_site);  // short Ls: many sites per CTA
+  if (spc < 1) spc = 1;
+  const int threads = nsg * spc;
+  const dim3 grid((unsigned)(2 * ((g.N4h + spc - 1) / spc)));  // (site block, parity), parity fastest
+  const size_t smem = (size_t)spc * per_site;
   const char* ps = static_cast<const char*>(psi);
   const char* ch = static_cast<const char*>(chi);
   const char* e = static_cast<const char*>(Ue);
   const char* o = static_cast<const char*>(Uo);
-#define FK(P_)                                                                   \
-  if (c12)                                                                       \
-    k_force<P_, true><<<blocks, threads, 0, st>>>(g, ps, ch, e, o, F, G, coef);        \
-  else                                                                           \
-    k_force<P_, false><<<blocks, threads, 0, st>>>(g, ps, ch, e, o, F, G, coef);
+#define FK(P_)                                                                                 \
+  if (c12)                                                                                     \
+    k_force<P_, true><<<grid, threads, smem, st>>>(g, ps, ch, e, o, F, G, coef, nsg, spc);    \
+  else                                                                                         \
+    k_force<P_, false><<<grid, threads, smem, st>>>(g, ps, ch, e, o, F, G, coef, nsg, spc);
   switch (prec) {
     case P64: FK(P64) break;
     case P32: FK(P32) break;
