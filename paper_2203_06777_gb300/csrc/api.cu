@@ -542,18 +542,29 @@ int cg_normal(grid_dwf_t* h, const void* rhs, void* xo_, double tol, int maxiter
   RET(ws_get(h, WS_CG_TO, hb, &to));
   const int P = GRID_DWF_FP64;
   CK(launch_reduce(P, rhs, nullptr, N, Ls, h->partials, h->scal, FIN_STORE, S_TMP1, h->stream), "cg norm");
-  // true residual r = rhs - A x_o
-  RET(mdagm_impl(h, P, xo, Ap, to, te));
-  flops += 4 * half_flops;
-  CK(launch_residual64(rhs, Ap, r, N, Ls, h->partials, h->scal, S_RR, h->stream), "cg residual");
+  CK(launch_reduce(P, xo, nullptr, N, Ls, h->partials, h->scal, FIN_STORE, S_TMP0, h->stream), "cg guess norm");
   RET(read_scalars(h));
   const double rhs_norm = std::sqrt(h->host_scal[S_TMP1]);
-  double rr = h->host_scal[S_RR];
+  double rr;
+  if (h->host_scal[S_TMP0] == 0.0) {
+    // zero initial guess: r = rhs exactly, no FP64 Mpc^+ Mpc needed
+    CK(launch_convert(P, P, rhs, r, N, Ls, nullptr, 1.0, h->stream), "cg residual");
+    rr = h->host_scal[S_TMP1];
+    RET(write_scalar(h, S_RR, rr));
+  } else {
+    // true residual r = rhs - A x_o
+    RET(mdagm_impl(h, P, xo, Ap, to, te));
+    flops += 4 * half_flops;
+    CK(launch_residual64(rhs, Ap, r, N, Ls, h->partials, h->scal, S_RR, h->stream), "cg residual");
+    RET(read_scalars(h));
+    rr = h->host_scal[S_RR];
+  }
   if (!is_finite(rr) || !is_finite(rhs_norm)) return fail(h, GRID_DWF_ERR_NONFINITE, "cg: non-finite source or guess");
   const double target = tol * rhs_norm;
   int iters = 0, updates = 0;
   bool converged = std::sqrt(rr) <= target;
   double true_res = rhs_norm > 0 ? std::sqrt(rr) / rhs_norm : 0.0;
+  bool rr_is_true = true;  // rr is the FP64 true residual of the current x_o (no recomputation needed)
 
   if (mode == GRID_DWF_CG_FP64) {
     RET(ws_get(h, WS_CG_P, hb, &p));
@@ -568,6 +579,7 @@ int cg_normal(grid_dwf_t* h, const void* rhs, void* xo_, double tol, int maxiter
       ++iters;
       RET(read_scalars(h));
       rr = h->host_scal[S_RR];
+      rr_is_true = false;  // the recursively updated residual
       if (!is_finite(rr)) return fail(h, GRID_DWF_ERR_NONFINITE, "cg: non-finite residual");
       converged = std::sqrt(rr) <= target;
     }
@@ -604,6 +616,7 @@ int cg_normal(grid_dwf_t* h, const void* rhs, void* xo_, double tol, int maxiter
       CK(launch_cg_xr(GRID_DWF_FP32, PS, xs, rs, ps, aps, N, Ls, h->partials, h->scal, h->stream), "cg update");
       flops += 4 * half_flops;
       ++iters;
+      rr_is_true = false;  // x_s has moved since the last true residual
       RET(read_scalars(h));
       const double rr_old_s = rr_s;  // |r_s|^2 before this step (the denominator of beta)
       rr_s = h->host_scal[S_RRNEW];
@@ -620,9 +633,10 @@ int cg_normal(grid_dwf_t* h, const void* rhs, void* xo_, double tol, int maxiter
         ++updates;
         const double rr64 = h->host_scal[S_TMP1];
         if (!is_finite(rr64)) return fail(h, GRID_DWF_ERR_NONFINITE, "cg: non-finite true residual");
+        rr = rr64;
+        rr_is_true = true;  // x_s was folded into x_o and zeroed: rr64 is the residual of x_o
         if (std::sqrt(rr64) <= target) {
           converged = true;
-          rr = rr64;
           break;
         }
         const double sigma_new = std::sqrt(nreal) / std::sqrt(rr64);
@@ -642,12 +656,17 @@ int cg_normal(grid_dwf_t* h, const void* rhs, void* xo_, double tol, int maxiter
       CK(launch_cg_p(GRID_DWF_FP32, PS, rs, ps, N, Ls, h->scal, h->stream), "cg p");
     }
   }
-  // final true residual of the normal equations, FP64
-  RET(mdagm_impl(h, P, xo, Ap, to, te));
-  flops += 4 * half_flops;
-  CK(launch_residual64(rhs, Ap, r, N, Ls, h->partials, h->scal, S_TMP0, h->stream), "cg final");
-  RET(read_scalars(h));
-  true_res = rhs_norm > 0 ? std::sqrt(h->host_scal[S_TMP0]) / rhs_norm : 0.0;
+  // final true residual of the normal equations, FP64 (already known when the loop ended on a
+  // reliable update or did not run)
+  double rr_final = rr;
+  if (!rr_is_true) {
+    RET(mdagm_impl(h, P, xo, Ap, to, te));
+    flops += 4 * half_flops;
+    CK(launch_residual64(rhs, Ap, r, N, Ls, h->partials, h->scal, S_TMP0, h->stream), "cg final");
+    RET(read_scalars(h));
+    rr_final = h->host_scal[S_TMP0];
+  }
+  true_res = rhs_norm > 0 ? std::sqrt(rr_final) / rhs_norm : 0.0;
   res.iters = iters;
   res.updates = updates;
   res.true_res = true_res;
