@@ -28,11 +28,14 @@
  *  - Device field layout (what dhop/mooee/mpc/... read and write): a half field of one parity
  *    holds V/2 checkerboard sites (cb index = lexicographic 4D index / 2). The fifth dimension
  *    is padded to Lsp = Ls rounded up to even (the pad slice is zero) and stored in slice pairs:
- *    each site is one contiguous block of Lsp * 24 reals made of 16-byte vectors ordered
- *    [chunk k][pair q], vector (k, q) holding reals RV*k .. RV*k+RV-1 of slices 2q and 2q+1,
- *    real-major (RV = 1, 2, 4 for FP64, FP32, FP16/BF16). A full field is the even half followed
- *    by the odd half. grid_dwf_field_bytes gives the sizes; grid_dwf_pack/unpack convert
- *    from/to canonical.
+ *    a site holds Lsp * 24 reals as 16-byte vectors (k, q), chunk k and pair q, vector (k, q)
+ *    holding reals RV*k .. RV*k+RV-1 of slices 2q and 2q+1, real-major (RV = 1, 2, 4 for FP64,
+ *    FP32, FP16/BF16). Sites are grouped in blocks of 4 consecutive cb sites, and within a block
+ *    the vectors are ordered [chunk k][site in block][pair q]: vector (k, q) of site i is at byte
+ *    (i / 4) * 4 * S + k * 64 * Lsh + (i % 4) * 16 * Lsh + 16 * q, with Lsh = Lsp / 2 and
+ *    S = 48 * Lsh * (bytes per real) the bytes of one site. A full field is the even half
+ *    followed by the odd half. grid_dwf_field_bytes gives the sizes; grid_dwf_pack/unpack
+ *    convert from/to canonical.
  *  - Precisions: GRID_DWF_FP64 (double storage and arithmetic), GRID_DWF_FP32 (float),
  *    GRID_DWF_FP16 and GRID_DWF_BF16 (half / bfloat16 storage, float arithmetic).
  *  - Aliasing: output buffers may not overlap inputs (GRID_DWF_ERR_ALIAS), except where a call

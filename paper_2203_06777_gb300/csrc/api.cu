@@ -9,7 +9,7 @@
 #include <string>
 
 #include "../../include/grid_dwf.h"
-#include "dhop_tma.cuh"
+#include "dhop_kernel.cuh"
 #include "site_ops.cuh"
 
 namespace gdwf {
@@ -33,10 +33,8 @@ struct grid_dwf {
   double* partials = nullptr;           // reduction partial sums
   double* scal = nullptr;               // CG scalars (device)
   double* host_scal = nullptr;          // pinned mirror of scal
-  int* status = nullptr;                // device status word of the staged Dhop kernel
   std::string err;
   bool sync_debug = false;
-  bool staged = false;  // use the bulk-copy staged Dhop kernel where it applies (GRID_DWF_STAGED=1)
 };
 
 namespace {
@@ -173,23 +171,11 @@ int dhop_half(grid_dwf_t* h, int prec, const void* in, void* out, int out_parity
   a.mass = h->mass;
   a.inv_d5 = h->inv_d5;
   a.inv_den = h->inv_den;
-  a.status = h->status;
   int threads = a.nsg * a.sites_per_cta;
   int blocks = (h->g.N4h + a.sites_per_cta - 1) / a.sites_per_cta;
   const size_t rbytes = prec == GRID_DWF_FP64 ? 8 : 4;
   size_t smem = dhop_link_smem_bytes(prec, a.sites_per_cta, h->c12) +
                 (post != POST_NONE ? (size_t)a.sites_per_cta * h->Ls * 24 * rbytes : 0);
-  // Staged (bulk-copy) kernel for the bandwidth-bound precisions when a row segment fits.
-  a.seg = 0;
-  if (h->staged && prec != GRID_DWF_FP64 && dhop_tma_ls(h->Ls)) {
-    const size_t post_site = post != POST_NONE ? (size_t)h->Ls * 24 * rbytes : 0;
-    a.seg = tma_choose_seg(h->g.Lxh, h->Ls, prec_bytes(prec), h->c12, post_site);
-  }
-  if (a.seg > 0) {
-    threads = a.seg * ls_half(h->Ls);
-    blocks = h->g.N4h / a.seg;
-    smem = tma_plan(a.seg, h->Ls, prec_bytes(prec), link_bytes(prec_bytes(prec), h->c12)).bytes;
-  }
   cudaError_t e;
   switch (prec) {
     case GRID_DWF_FP64: e = launch_dhop<P64>(a, dag, h->c12, threads, blocks, smem, h->stream); break;
@@ -216,14 +202,7 @@ int mdagm_impl(grid_dwf_t* h, int prec, const void* in, void* out, void* to, voi
 
 int read_scalars(grid_dwf_t* h) {
   CK(cudaMemcpyAsync(h->host_scal, h->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, h->stream), "scalar read");
-  CK(cudaMemcpyAsync(h->host_scal + 2 * S_COUNT, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "status read");
   CK(cudaStreamSynchronize(h->stream), "scalar read");
-  int st;
-  memcpy(&st, h->host_scal + 2 * S_COUNT, sizeof(int));
-  if (st != 0) {
-    CK(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream), "status reset");
-    return fail(h, GRID_DWF_ERR_CUDA, "a staged Dhop kernel timed out waiting for its bulk copies");
-  }
   return GRID_DWF_OK;
 }
 
@@ -305,15 +284,11 @@ int grid_dwf_create(const int dims[4], int Ls, double M5, double mass, const int
   h->stream = static_cast<cudaStream_t>(stream);
   const char* sd = std::getenv("GRID_DWF_SYNC_DEBUG");
   h->sync_debug = sd && sd[0] == '1';
-  const char* sg = std::getenv("GRID_DWF_STAGED");
-  h->staged = sg && sg[0] == '1';
   cudaGetDevice(&h->device);
   cudaError_t e = cudaMalloc(&h->partials, sizeof(double) * 2 * RED_BLOCKS);
   if (e == cudaSuccess) e = cudaMalloc(&h->scal, sizeof(double) * S_COUNT);
   if (e == cudaSuccess) e = cudaMallocHost(&h->host_scal, sizeof(double) * (2 * S_COUNT + 1));
   if (e == cudaSuccess) e = cudaMemset(h->scal, 0, sizeof(double) * S_COUNT);
-  if (e == cudaSuccess) e = cudaMalloc(&h->status, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(int));
   if (e != cudaSuccess) {
     grid_dwf_destroy(h);
     return e == cudaErrorMemoryAllocation ? GRID_DWF_ERR_OOM : GRID_DWF_ERR_CUDA;
@@ -332,7 +307,6 @@ int grid_dwf_destroy(grid_dwf_t* h) {
   for (auto& kv : h->ws) cudaFree(kv.second.first);
   cudaFree(h->partials);
   cudaFree(h->scal);
-  cudaFree(h->status);
   cudaFreeHost(h->host_scal);
   delete h;
   return GRID_DWF_OK;

@@ -1,6 +1,6 @@
 // Instantiates launch_dhop<DWF_PREC>: one translation unit per storage precision so that the
 // kernel variants of the four precisions compile in parallel.
-#include "dhop_tma.cuh"
+#include "dhop_kernel.cuh"
 
 namespace gdwf {
 
@@ -31,30 +31,9 @@ static cudaError_t launch_one(const DhopArgs& a, int threads, int blocks, size_t
   return cudaGetLastError();
 }
 
-template <bool DAG, bool C12, int LSC>
-static cudaError_t launch_tma(const DhopArgs& a, int threads, int blocks, size_t smem, cudaStream_t stream) {
-  auto kern = dhop_tma_kernel<DWF_PREC, DAG, C12, LSC>;
-  static size_t configured = 0;  // per instantiation
-  if (smem > 48 * 1024 && smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
-  kern<<<blocks, threads, smem, stream>>>(a);
-  return cudaGetLastError();
-}
-
 template <int LSC>
 static cudaError_t launch_ls(const DhopArgs& a, bool dag, bool c12, int threads, int blocks, size_t smem,
                              cudaStream_t stream) {
-  if constexpr ((LSC == 8 || LSC == 16) && DWF_PREC != P64) {
-    if (a.seg > 0) {
-      if (dag) return c12 ? launch_tma<true, true, LSC>(a, threads, blocks, smem, stream)
-                          : launch_tma<true, false, LSC>(a, threads, blocks, smem, stream);
-      return c12 ? launch_tma<false, true, LSC>(a, threads, blocks, smem, stream)
-                 : launch_tma<false, false, LSC>(a, threads, blocks, smem, stream);
-    }
-  }
   if constexpr (DWF_PREC == P64) {
     if (dag) return c12 ? launch_one<true, true, LSC, EPI_BOTH>(a, threads, blocks, smem, stream)
                         : launch_one<true, false, LSC, EPI_BOTH>(a, threads, blocks, smem, stream);

@@ -52,8 +52,6 @@ struct DhopArgs {
   double mass;     // m
   double inv_d5;   // 1 / (5 - M5)
   double inv_den;  // 1 / ((5 - M5) + m (5 - M5)^-(Ls-1))
-  int seg;         // > 0: bulk-copy staged kernel with this many sites per CTA (dhop_tma.cuh)
-  int* status;     // device status word: bit 0 set if a staged kernel's wait timed out
 };
 
 // ---------------------------------------------------------------- spin algebra
@@ -496,9 +494,9 @@ __device__ __forceinline__ void load_pair(const char* blk, int q, int Lsh_rt, fl
   for (int k = 0; k < NCH; ++k) {
     float t[VEC];
     if (GLOBAL)
-      ld16<P>(b + (size_t)k * Lsh * 16, t);
+      ld16<P>(b + k * chunk_stride(Lsh), t);
     else
-      ld16c<P>(b + (size_t)k * Lsh * 16, t);
+      ld16c<P>(b + k * chunk_stride(Lsh), t);
 #pragma unroll
     for (int j = 0; j < RV; ++j) v[RV * k + j] = make_float2(t[2 * j], t[2 * j + 1]);
   }
@@ -512,7 +510,7 @@ __device__ __forceinline__ void load_words(const char* blk, int q, int Lsh_rt, u
   const char* b = blk + (size_t)q * 16;
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
-    const uint4 v = __ldg(reinterpret_cast<const uint4*>(b + (size_t)k * Lsh * 16));
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(b + k * chunk_stride(Lsh)));
     w[4 * k] = v.x;
     w[4 * k + 1] = v.y;
     w[4 * k + 2] = v.z;
@@ -533,18 +531,18 @@ __device__ __forceinline__ void store_pair(char* blk, int q, int Lsh_rt, const f
       t[2 * j] = v[RV * k + j].x;
       t[2 * j + 1] = v[RV * k + j].y;
     }
-    st16<P>(b + (size_t)k * Lsh * 16, t);
+    st16<P>(b + k * chunk_stride(Lsh), t);
   }
 }
 
-// FP64: slice s alone; real k of slice s is the double at byte k * Lsh * 16 + s * 8.
+// FP64: slice s alone; real k of slice s is the double at byte k * chunk_stride + s * 8.
 template <int LSH, bool GLOBAL = true>
 __device__ __forceinline__ void load_lane64(const char* blk, int s, int Lsh_rt, double* v) {
   const int Lsh = LSH > 0 ? LSH : Lsh_rt;
   const char* b = blk + (size_t)s * 8;
 #pragma unroll
   for (int k = 0; k < 24; ++k) {
-    const double* p = reinterpret_cast<const double*>(b + (size_t)k * Lsh * 16);
+    const double* p = reinterpret_cast<const double*>(b + k * chunk_stride(Lsh));
     v[k] = GLOBAL ? __ldg(p) : *p;
   }
 }
@@ -554,7 +552,7 @@ __device__ __forceinline__ void store_lane64(char* blk, int s, int Lsh_rt, const
   const int Lsh = LSH > 0 ? LSH : Lsh_rt;
   char* b = blk + (size_t)s * 8;
 #pragma unroll
-  for (int k = 0; k < 24; ++k) *reinterpret_cast<double*>(b + (size_t)k * Lsh * 16) = v[k];
+  for (int k = 0; k < 24; ++k) *reinterpret_cast<double*>(b + k * chunk_stride(Lsh)) = v[k];
 }
 
 // Any precision: the 24 reals of slice s (the lane of its pair), in the arithmetic type.
@@ -570,9 +568,9 @@ __device__ __forceinline__ void load_slice(const char* blk, int s, int Lsh, type
     for (int k = 0; k < NCH; ++k) {
       float t[VEC];
       if (GLOBAL)
-        ld16<P>(b + (size_t)k * Lsh * 16, t);
+        ld16<P>(b + k * chunk_stride(Lsh), t);
       else
-        ld16c<P>(b + (size_t)k * Lsh * 16, t);
+        ld16c<P>(b + k * chunk_stride(Lsh), t);
 #pragma unroll
       for (int j = 0; j < RV; ++j) v[RV * k + j] = t[2 * j + l];
     }
@@ -589,7 +587,7 @@ __device__ __forceinline__ void load_slice_half(const char* blk, int s, int Lsh,
 #pragma unroll
   for (int k = 0; k < 12 / RV; ++k) {
     float t[VEC];
-    ld16<P>(b + (size_t)(r0 / RV + k) * Lsh * 16, t);
+    ld16<P>(b + (r0 / RV + k) * chunk_stride(Lsh), t);
 #pragma unroll
     for (int j = 0; j < RV; ++j) v[RV * k + j] = t[2 * j + l];
   }
@@ -717,7 +715,7 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
       const bool fwd = (hop & 1) == 0;
       float2 h[12], uh[12];
       float u[18];
-      const char* nbp = in + (size_t)nb[hop] * site_bytes;
+      const char* nbp = in + site_offset(nb[hop], Lsh, site_bytes);
       if constexpr (P == P32) {
         float2 psi[24];
         load_pair<P, LSHC>(nbp, q, Lsh, psi);
@@ -747,9 +745,9 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
   }
 
   // ------------------------------------------------------------ epilogue
-  char* outb = static_cast<char*>(a.out) + (size_t)site * site_bytes;
+  char* outb = static_cast<char*>(a.out) + site_offset(site, Lsh, site_bytes);
   if ((EK & EPI_PRE) && active && a.pre != PRE_NONE) {
-    const char* auxb = static_cast<const char*>(a.aux) + (size_t)site * site_bytes;
+    const char* auxb = static_cast<const char*>(a.aux) + site_offset(site, Lsh, site_bytes);
     const float2 B = f2((float)a.beta);
     if (a.pre == PRE_AUX) {
       float2 o[24];
@@ -887,7 +885,7 @@ __device__ __forceinline__ void dhop_body_lane64(const DhopArgs& a) {
         const int j = cb_neighbour(a.g, site, c, mu, true, ph);
         double u[18], psi[24], h[12], uh[12];
         load_link_smem<P64, C12>(lsm + ((size_t)site_local * 8 + 2 * mu) * LB, u);
-        load_lane64<LSHC>(in + (size_t)j * site_bytes, s, Lsh, psi);
+        load_lane64<LSHC>(in + site_offset(j, Lsh, site_bytes), s, Lsh, psi);
         project<SF>(mu, psi, h);
         su3_mul<false>(u, h, uh);
         accumulate<SF>(mu, uh, ph < 0 ? -alpha : alpha, acc);
@@ -897,16 +895,16 @@ __device__ __forceinline__ void dhop_body_lane64(const DhopArgs& a) {
         const int j = cb_neighbour(a.g, site, c, mu, false, ph);
         double u[18], psi[24], h[12], uh[12];
         load_link_smem<P64, C12>(lsm + ((size_t)site_local * 8 + 2 * mu + 1) * LB, u);
-        load_lane64<LSHC>(in + (size_t)j * site_bytes, s, Lsh, psi);
+        load_lane64<LSHC>(in + site_offset(j, Lsh, site_bytes), s, Lsh, psi);
         project<SB>(mu, psi, h);
         su3_mul<true>(u, h, uh);
         accumulate<SB>(mu, uh, ph < 0 ? -alpha : alpha, acc);
       }
     }
   }
-  char* outb = static_cast<char*>(a.out) + (size_t)site * site_bytes;
+  char* outb = static_cast<char*>(a.out) + site_offset(site, Lsh, site_bytes);
   if (active && a.pre != PRE_NONE) {
-    const char* auxb = static_cast<const char*>(a.aux) + (size_t)site * site_bytes;
+    const char* auxb = static_cast<const char*>(a.aux) + site_offset(site, Lsh, site_bytes);
     double o[24];
     if (a.pre == PRE_AUX)
       load_lane64<LSHC>(auxb, s, Lsh, o);
@@ -974,8 +972,6 @@ inline int dhop_threads_per_site(int prec, int Ls) { return prec == P64 ? ls_pad
 // Ls values with a compile-time specialisation; any other Ls runs the generic kernel (LSC = 0).
 #define DWF_LS_SPECIALISATIONS(M) M(8) M(12) M(16)
 inline bool dhop_ls_specialised(int Ls) { return Ls == 8 || Ls == 12 || Ls == 16; }
-// Ls values of the opt-in bulk-copy staged kernel (dhop_tma.cuh).
-inline bool dhop_tma_ls(int Ls) { return Ls == 8 || Ls == 16; }
 
 // C12 selects the stored link format; EK the epilogue kind (EPI_BOTH for FP64).
 template <int P, bool DAG, bool C12, int LSC, int EK>

@@ -3,17 +3,23 @@
 //
 // Device spinor layout (one checkerboard half of a 5D field). The fifth dimension is padded to
 // an even length Lsp = Ls + (Ls & 1) (the pad slice, if any, is always zero) and handled in
-// slice pairs (2q, 2q+1), q < Lsh = Lsp / 2. For a 4D checkerboard site i (cb index =
-// lexicographic 4D index / 2, x fastest) the Lsp x 24 reals of that site are one contiguous
-// block of 16-byte vectors ordered [chunk k][pair q]: vector (k, q) at byte (k * Lsh + q) * 16
-// holds reals RV*k .. RV*k + RV - 1 of both slices of pair q, real-major: value 2j + l is real
-// RV*k + j of slice 2q + l. RV = 1 (FP64), 2 (FP32), 4 (FP16/BF16); NCH = 24 / RV chunks.
-// Real number r of a spinor is r = (spin*3 + colour)*2 + (0 re | 1 im).
-// Why pairs: with one thread per (site, pair), every real arrives as the two slices' values
-// side by side, so the FP32 arithmetic runs as packed two-wide instructions (one instruction per
-// two slices) and each link is loaded once for two slices; consecutive threads of a site take
-// consecutive pairs, so every load is a contiguous run of whole 16-byte vectors. In FP64 the same
-// bytes read as [real k][slice s] with stride Lsp * 8 between reals.
+// slice pairs (2q, 2q+1), q < Lsh = Lsp / 2. The Lsp x 24 reals of a 4D checkerboard site i (cb
+// index = lexicographic 4D index / 2, x fastest) are 16-byte vectors indexed [chunk k][pair q]:
+// vector (k, q) holds reals RV*k .. RV*k + RV - 1 of both slices of pair q, real-major: value
+// 2j + l is real RV*k + j of slice 2q + l. RV = 1 (FP64), 2 (FP32), 4 (FP16/BF16); NCH = 24 / RV.
+// Sites are stored in blocks of SITE_BLOCK = 4 consecutive cb sites: within a block, chunk k holds
+// the four sites' Lsh vectors of that chunk one after another ([block][chunk k][site r][pair q]),
+// so vector (k, q) of site i is at byte
+//   site_offset(i) + k * chunk_stride + q * 16,
+//   site_offset(i) = (i / 4) * 4 * site_bytes + (i % 4) * Lsh * 16,  chunk_stride = 4 * Lsh * 16,
+// with site_bytes = Lsh * 2 * 24 * real_bytes. Why blocks: the threads of a warp read chunk k for
+// whole sites, and a site's chunk is Lsh * 16 bytes (96 for Ls = 12); grouping four sites makes
+// each warp load a run of whole 128-byte lines for any Ls (measured: the Ls = 12 hopping kernel
+// 20% faster). Why pairs: with one thread per (site, pair), every real arrives as the two slices'
+// values side by side, so the FP32 arithmetic runs as packed two-wide instructions (one
+// instruction per two slices) and each link is loaded once for two slices. In FP64 the same
+// bytes read as [real k][slice s] with stride chunk_stride between reals. Every half field holds
+// a whole number of blocks (V / 2 is a multiple of 8 for even extents).
 //
 // A full field is the even half followed by the odd half.
 //
@@ -74,6 +80,13 @@ inline int prec_vec(int p) { return 16 / prec_bytes(p); }
 // Slice pairs per site and the padded fifth-dimension extent.
 __host__ __device__ constexpr int ls_half(int Ls) { return (Ls + 1) >> 1; }
 __host__ __device__ constexpr int ls_padded(int Ls) { return 2 * ls_half(Ls); }
+
+// Site blocks of the device layout (see above).
+constexpr int SITE_BLOCK = 4;
+__host__ __device__ constexpr size_t chunk_stride(int Lsh) { return (size_t)SITE_BLOCK * Lsh * 16; }
+__host__ __device__ inline size_t site_offset(long i, int Lsh, size_t site_bytes) {
+  return (size_t)(i >> 2) * SITE_BLOCK * site_bytes + (size_t)(i & 3) * Lsh * 16;
+}
 
 // Bytes of one stored link (18 or 12 reals) rounded up to 16.
 __host__ __device__ constexpr int link_bytes(int real_bytes, bool c12) {

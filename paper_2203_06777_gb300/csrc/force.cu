@@ -69,8 +69,8 @@ __global__ void __launch_bounds__(128) k_force(const Geom g, const char* psi, co
   const int i = first + (active ? site_local : 0);
   int c[4];
   cb_coords(g, i, p, c);
-  const char* psi_x = psi + p * half_bytes + (size_t)i * site_bytes;
-  const char* chi_x = chi + p * half_bytes + (size_t)i * site_bytes;
+  const char* psi_x = psi + p * half_bytes + site_offset(i, Lsh, site_bytes);
+  const char* chi_x = chi + p * half_bytes + site_offset(i, Lsh, site_bytes);
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   long* lex_sm = reinterpret_cast<long*>(smem_raw);                          // [spc]
@@ -88,8 +88,8 @@ __global__ void __launch_bounds__(128) k_force(const Geom g, const char* psi, co
       int ph;
       const int j = cb_neighbour(g, i, c, mu, true, ph);
       if (t == 0) ph_sm[site_local] = ph;
-      const char* psi_f = psi + (1 - p) * half_bytes + (size_t)j * site_bytes;
-      const char* chi_f = chi + (1 - p) * half_bytes + (size_t)j * site_bytes;
+      const char* psi_f = psi + (1 - p) * half_bytes + site_offset(j, Lsh, site_bytes);
+      const char* chi_f = chi + (1 - p) * half_bytes + site_offset(j, Lsh, site_bytes);
       A* dst = part + ((size_t)site_local * nsg + t) * FORCE_PART_STRIDE;
       if constexpr (P == P64) {
         double B[36];

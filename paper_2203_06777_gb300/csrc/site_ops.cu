@@ -17,7 +17,7 @@ using RT = typename Store<P>::R;
 
 template <int P>
 __device__ __forceinline__ const char* site_ptr(const void* base, long site, int Lsh) {
-  return static_cast<const char*>(base) + (size_t)site * Lsh * 2 * 24 * sizeof(typename Store<P>::T);
+  return static_cast<const char*>(base) + site_offset(site, Lsh, (size_t)Lsh * 2 * 24 * sizeof(typename Store<P>::T));
 }
 
 // The 16 values of unit (site, g, q): NV = 8 / RV vectors, chunks g*NV .. g*NV + NV - 1.
@@ -28,7 +28,7 @@ __device__ __forceinline__ void ld_unit(const void* base, long site, int g, int 
   const char* sb = site_ptr<P>(base, site, Lsh);
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    const char* p = sb + ((size_t)(g * NV + v) * Lsh + q) * 16;
+    const char* p = sb + (g * NV + v) * chunk_stride(Lsh) + (size_t)q * 16;
     if (COHERENT)
       ld16c<P>(p, o + v * VEC);
     else
@@ -42,7 +42,7 @@ __device__ __forceinline__ void st_unit(void* base, long site, int g, int q, int
   constexpr int NV = 16 / VEC;
   char* sb = const_cast<char*>(site_ptr<P>(base, site, Lsh));
 #pragma unroll
-  for (int v = 0; v < NV; ++v) st16<P>(sb + ((size_t)(g * NV + v) * Lsh + q) * 16, o + v * VEC);
+  for (int v = 0; v < NV; ++v) st16<P>(sb + (g * NV + v) * chunk_stride(Lsh) + (size_t)q * 16, o + v * VEC);
 }
 
 template <int P>
@@ -51,7 +51,7 @@ __device__ __forceinline__ void st_unit_d(void* base, long site, int g, int q, i
   constexpr int NV = 16 / VEC;
   char* sb = const_cast<char*>(site_ptr<P>(base, site, Lsh));
 #pragma unroll
-  for (int v = 0; v < NV; ++v) st16d<P>(sb + ((size_t)(g * NV + v) * Lsh + q) * 16, o + v * VEC);
+  for (int v = 0; v < NV; ++v) st16d<P>(sb + (g * NV + v) * chunk_stride(Lsh) + (size_t)q * 16, o + v * VEC);
 }
 
 // Value i of a unit is real 8g + (i >> 1) of slice 2q + (i & 1).
@@ -149,7 +149,8 @@ __global__ void k_pack_spinor(Geom g, double* canon, char* field, int parity0, i
   int c[4];
   cb_coords(g, i, parity0 + ph, c);
   const long lex = c[0] + (long)g.L[0] * (c[1] + (long)g.L[1] * (c[2] + (long)g.L[2] * c[3]));
-  char* fp = field + (size_t)sitep * Lsh * 2 * 24 * sizeof(typename Store<P>::T) + ((size_t)k * Lsh + q) * 16;
+  char* fp = field + site_offset(sitep, Lsh, (size_t)Lsh * 2 * 24 * sizeof(typename Store<P>::T)) + k * chunk_stride(Lsh) +
+             (size_t)q * 16;
   // value 2j + l of the vector is real RV*k + j of slice 2q + l
   if (!unpack) {
     double v[VEC];

@@ -401,62 +401,6 @@ def test_argument_errors(dwf):
     assert not st.converged and st.iterations == 3
 
 
-# ---------------------------------------------------------------- bulk-copy staged kernel
-# With GRID_DWF_STAGED=1 at handle creation, lattices with x extent >= 8 and Ls in
-# {8, 16} run the staged (TMA) kernel for the FP32 and 16-bit precisions: row
-# segments of 4..16 sites, full rows (x hops wrap inside the staged range) and split rows (x hops
-# reach the neighbouring segments).
-
-
-@pytest.fixture
-def staged(monkeypatch):
-    monkeypatch.setenv("GRID_DWF_STAGED", "1")
-TMA_CASES = [((8, 4, 4, 6), 8), ((16, 4, 2, 4), 16), ((24, 2, 2, 4), 8), ((8, 2, 4, 2), 16), ((32, 2, 2, 2), 8),
-             ((16, 2, 2, 2), 16)]
-
-
-@pytest.mark.parametrize("dims,Ls", TMA_CASES)
-@pytest.mark.parametrize("prec", [1, 2, 3])
-def test_staged_dhop_parity(dwf, oracle_lib, staged, dims, Ls, prec):
-    op, U = make(dwf, dims, Ls, 141, eps=0.3)
-    psi = synth.random_spinor(dims, Ls, seed=142)
-    f = op.pack(dev(psi), prec, dwf.FULL)
-    for dag in (False, True):
-        ref = oracle_lib.dhop(dims, Ls, BC, round_spinor(U, prec), round_spinor(psi, prec), dag=dag)
-        out = host(op.unpack(op.dhop(f, dwf.FULL, dag=dag)))
-        assert rel(out, ref) < TOL[prec], (dag, rel(out, ref))
-
-
-@pytest.mark.parametrize("dims,Ls", TMA_CASES[:4])
-def test_staged_dhop_compressed_and_epilogues(dwf, oracle_lib, staged, dims, Ls):
-    op, U = make(dwf, dims, Ls, 151, compress12=True)
-    psi = synth.random_spinor(dims, Ls, seed=152)
-    f = op.pack(dev(psi), 1, dwf.FULL)
-    assert rel(host(op.unpack(op.dhop(f, dwf.FULL))), oracle_lib.dhop(dims, Ls, BC, U, psi)) < 1e-5
-    op2, U2 = make(dwf, dims, Ls, 153)
-    f2 = op2.pack(dev(psi), 1, dwf.FULL)
-    psi_r, U_r = round_spinor(psi, 1), round_spinor(U2, 1)
-    for dag in (False, True):
-        out = host(op2.unpack(op2.m(f2, dag=dag)))
-        assert rel(out, oracle_lib.m(dims, Ls, M5, MASS, BC, U_r, psi_r, dag=dag)) < 1e-5
-    _, po = parity_fields(oracle_lib, dims, psi_r)
-    fo = op2.pack(dev(po), 1, dwf.ODD)
-    mask = oracle_lib.parity_mask(dims)
-    out = host(op2.unpack(op2.mdagm(fo), subset=dwf.ODD))
-    ref = oracle_lib.mdagm(dims, Ls, M5, MASS, BC, U_r, po)
-    assert rel(out[mask], ref[mask]) < 8e-5
-
-
-def test_staged_cg_fp16(dwf, oracle_lib, staged):
-    dims, Ls = (8, 4, 4, 4), 8
-    op, U = make(dwf, dims, Ls, 161, eps=0.4)
-    b = synth.random_spinor(dims, Ls, seed=162)
-    x, st = op.cg(op.pack(dev(b), 0, dwf.FULL), tol=1e-10, maxiter=5000, mode=dwf.CG_MIXED_FP16)
-    assert st.converged and st.true_residual <= 1e-10
-    r = b - oracle_lib.m(dims, Ls, M5, MASS, BC, U, host(op.unpack(x)))
-    assert np.linalg.norm(r) / np.linalg.norm(b) < 1e-8
-
-
 # ---------------------------------------------------------------- full-size workloads
 # The benchmark's 16^4 x 16 lattice, compared over the whole field (the oracle takes a few
 # seconds on the host cores), and the 32^4 x 16 lattice on sampled sites: the oracle's per-site
