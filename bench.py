@@ -209,15 +209,24 @@ def make_sets(dwf, torch, spec, prec, nsets, seed0):
     return sets
 
 
+def launches_per_step(op, prec, dwf) -> int:
+    """Kernel launches of one full-lattice Dhop: the packed precisions run both halves in one
+    launch (plus one tail launch when sites-per-CTA does not divide the half lattice); FP64 one
+    launch per half."""
+    if prec == dwf.FP64:
+        return 2
+    lsh = (op.Ls + 1) // 2
+    spc = min(max(1, 128 // lsh), op.half_sites)
+    return 1 if op.half_sites % spc == 0 else 2
+
+
 def time_dhop(dwf, torch, sets, steps, warmup, world):
-    """Time `steps` full-lattice Dhop applications (2 kernel launches each) with CUDA events."""
-    half = sets[0][0].half_reals
+    """Time `steps` full-lattice Dhop applications (DhopEO + DhopOE, one call each) with CUDA events."""
     stream = torch.cuda.current_stream()
 
     def step(i):
         op, src, dst = sets[i % len(sets)]
-        op.dhop(src[half:], dwf.EVEN, out=dst[:half])
-        op.dhop(src[:half], dwf.ODD, out=dst[half:])
+        op.dhop(src, dwf.FULL, out=dst)
 
     for i in range(warmup):
         step(i)
@@ -231,7 +240,7 @@ def time_dhop(dwf, torch, sets, steps, warmup, world):
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
-    return e0.elapsed_time(e1) / 1e3, 2 * steps
+    return e0.elapsed_time(e1) / 1e3
 
 
 def time_dhop_e2e(dwf, torch, sets, steps, warmup, world):
@@ -241,7 +250,6 @@ def time_dhop_e2e(dwf, torch, sets, steps, warmup, world):
     two device buffer sets alternate, so step i's transfers overlap step i-1's and i+1's
     compute; events order every buffer reuse. Timed from the first copy to the last result."""
     op, src, dst = sets[0]
-    half = op.half_reals
     nbuf = 2
     host_in = [torch.empty(src.shape, dtype=src.dtype, pin_memory=True) for _ in range(nbuf)]
     host_out = [torch.empty(dst.shape, dtype=dst.dtype, pin_memory=True) for _ in range(nbuf)]
@@ -265,8 +273,7 @@ def time_dhop_e2e(dwf, torch, sets, steps, warmup, world):
         with torch.cuda.stream(s_cmp):
             s_cmp.wait_event(ev_in[b])
             s_cmp.wait_event(ev_out[b])  # dev_out[b] has been copied back
-            op.dhop(dev_in[b][half:], dwf.EVEN, out=dev_out[b][:half])
-            op.dhop(dev_in[b][:half], dwf.ODD, out=dev_out[b][half:])
+            op.dhop(dev_in[b], dwf.FULL, out=dev_out[b])
             ev_done[b].record(s_cmp)
         with torch.cuda.stream(s_d2h):
             s_d2h.wait_event(ev_done[b])
@@ -364,7 +371,7 @@ def run_force(dwf, torch, spec, reps=20):
     return {"workload": "dwf_16x16x16x16_ls16_haar", "ms_per_force": round(ms, 4), "reps": reps,
             "precision": "fp32 fields, fp64 accumulation across blocks of 8 slice pairs",
             "ms_per_force_fp64": round(ms64, 4),
-            "includes": "M psi (2 fused Dhop+Mooee launches), |M psi|^2, force and ambient-gradient kernel"}
+            "includes": "M psi (one launch: Dhop with the fused Mooee term, both halves), |M psi|^2, force and ambient-gradient kernel"}
 
 
 def run_pf_force(dwf, torch, spec):
@@ -414,19 +421,17 @@ def run_sweep32(dwf, torch, steps=20, warmup=3):
         half = op.half_reals
         n = steps if name != "f64" else max(2, steps // 10)
         for _ in range(warmup):
-            op.dhop(src[half:], dwf.EVEN, out=dst[:half])
-            op.dhop(src[:half], dwf.ODD, out=dst[half:])
+            op.dhop(src, dwf.FULL, out=dst)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(n):
-            op.dhop(src[half:], dwf.EVEN, out=dst[:half])
-            op.dhop(src[:half], dwf.ODD, out=dst[half:])
+            op.dhop(src, dwf.FULL, out=dst)
         e1.record(stream)
         torch.cuda.synchronize()
-        per_launch = e0.elapsed_time(e1) / 1e3 / (2 * n)
-        gbs = algorithmic_bytes_per_site(rb, Ls) * n5 / per_launch / 1e9
-        rec = {"us_per_launch": round(per_launch * 1e6, 2), "gflops": round(FLOPS_PER_SITE * n5 / per_launch / 1e9, 1),
+        per_half = e0.elapsed_time(e1) / 1e3 / (2 * n)  # per half-lattice application
+        gbs = algorithmic_bytes_per_site(rb, Ls) * n5 / per_half / 1e9
+        rec = {"us_per_half_lattice": round(per_half * 1e6, 2), "gflops": round(FLOPS_PER_SITE * n5 / per_half / 1e9, 1),
                "algorithmic_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4)}
         if name == "f64":
             rec["alu_frac"] = round(rec["gflops"] / (FP64_ALU_TFLOPS * 1e3), 4)
@@ -517,23 +522,25 @@ def gpu_arm(args):
         steps = args.steps if name != "f64" else max(3, args.steps // 40)
         if name == "f32":
             with ClockSampler(torch.cuda.current_device()) as cs:
-                secs, launches = time_dhop(dwf, torch, sets, steps, args.warmup, world)
+                secs = time_dhop(dwf, torch, sets, steps, args.warmup, world)
             clocks = cs.summary()
         else:
-            secs, launches = time_dhop(dwf, torch, sets, steps, args.warmup, world)
+            secs = time_dhop(dwf, torch, sets, steps, args.warmup, world)
         secs = reduce_max(secs, world)
-        per_launch = secs / launches
+        launches = steps * launches_per_step(sets[0][0], prec, dwf)
+        per_step = secs / steps
         bytes_site = algorithmic_bytes_per_site(rb, Ls)
-        gbs = bytes_site * n5 / per_launch / 1e9
-        gflops = FLOPS_PER_SITE * n5 / per_launch / 1e9
+        gbs = bytes_site * 2 * n5 / per_step / 1e9
+        gflops = FLOPS_PER_SITE * 2 * n5 / per_step / 1e9
         rec = {"gflops": round(gflops, 1), "algorithmic_gbs": round(gbs, 1),
-               "hbm_frac": round(gbs / hbm_peak, 4), "us_per_launch": round(per_launch * 1e6, 2),
+               "hbm_frac": round(gbs / hbm_peak, 4), "us_per_step": round(per_step * 1e6, 2),
+               "us_per_half_lattice": round(per_step / 2 * 1e6, 2), "launches_per_step": launches // steps,
                "bytes_per_site": bytes_site, "steps": steps}
         if name == "f64":
             rec["alu_frac"] = round(gflops / (FP64_ALU_TFLOPS * 1e3), 4)
             rec["bound"] = "alu"
             rec["alu_peak_gflops"] = FP64_ALU_TFLOPS * 1e3
-        results[name] = (secs, steps, launches, per_launch, gbs, gflops)
+        results[name] = (secs, steps, launches, per_step, gbs, gflops)
         variants[name] = rec
         if name == "f32":
             e2e_steps = max(3, args.steps // 20)
@@ -549,7 +556,7 @@ def gpu_arm(args):
         if rank == 0:
             print(json.dumps({"variants": variants}), flush=True)
         return
-    secs, steps, launches, per_launch, gbs, gflops = results["f32"]
+    secs, steps, launches, per_step, gbs, gflops = results["f32"]
     value = job_throughput(FLOPS_PER_SITE * 2 * n5 * steps, world, secs) / 1e9
     line = {
         "metric": METRIC,
@@ -565,12 +572,12 @@ def gpu_arm(args):
         "dtype": "f32",
         "data": "synthetic (seeded exp(0.3 i H) links, Gaussian spinors)",
         "config": {"workload": WORKLOAD, "lattice": list(dims), "Ls": Ls, "M5": spec["M5"], "mass": spec["mass"],
-                   "bc": list(BC), "step": "DhopEO + DhopOE", "parallelism": f"replicas x{world}",
+                   "bc": list(BC), "step": "DhopEO + DhopOE (one full-lattice launch)", "parallelism": f"replicas x{world}",
                    "l2": "3 rotating operator+field sets (663 MB FP32) > L2"},
         "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                      "frac": round(gbs / hbm_peak, 4), "traffic": measured_traffic(), "peak_kind": peak_kind,
-                     "kernel": "dhop_kernel<FP32> (DhopEO / DhopOE)",
-                     "bytes_per_launch": algorithmic_bytes_per_site(4, Ls) * n5,
+                     "kernel": "dhop_kernel<FP32> (DhopEO + DhopOE in one launch)",
+                     "bytes_per_launch": algorithmic_bytes_per_site(4, Ls) * 2 * n5,
                      "source_hash": kernel_source_hash()},
         "variants": variants,
         "e2e": e2e,

@@ -148,9 +148,14 @@ int ensure_gauge(grid_dwf_t* h, int prec) {
 
 // One half-lattice hopping application with its fused epilogue.
 int dhop_half(grid_dwf_t* h, int prec, const void* in, void* out, int out_parity, bool dag, int pre, int post,
-              double alpha, double beta, const void* aux) {
+              double alpha, double beta, const void* aux, const void* in2 = nullptr, void* out2 = nullptr,
+              const void* aux2 = nullptr) {
   RET(ensure_gauge(h, prec));
   DhopArgs a;
+  a.in2 = in2;
+  a.out2 = out2;
+  a.aux2 = aux2;
+  a.blocks1 = 0;
   a.in = in;
   a.out = out;
   a.aux = aux;
@@ -185,6 +190,19 @@ int dhop_half(grid_dwf_t* h, int prec, const void* in, void* out, int out_parity
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "dhop launch");
   return GRID_DWF_OK;
+}
+
+// Both halves of a full-lattice hop (each output half from the other input half, independent):
+// one launch for the packed precisions (one ramp-up and tail instead of two), two for FP64.
+int dhop_full(grid_dwf_t* h, int prec, const char* in, char* out, bool dag, int pre, double alpha, double beta,
+              const char* aux) {
+  const size_t hb = half_bytes(h, prec);
+  if (prec == GRID_DWF_FP64) {
+    RET(dhop_half(h, prec, in + hb, out, 0, dag, pre, POST_NONE, alpha, beta, aux));
+    return dhop_half(h, prec, in, out + hb, 1, dag, pre, POST_NONE, alpha, beta, aux ? aux + hb : nullptr);
+  }
+  return dhop_half(h, prec, in + hb, out, 0, dag, pre, POST_NONE, alpha, beta, aux, in, out + hb,
+                   aux ? aux + hb : nullptr);
 }
 
 // out_o = Mpc in_o (dag: Mpc^+), via t_e = Mooee^-1 D_eo in and out = Mooee in - D_oe t_e / 4.
@@ -383,11 +401,8 @@ int grid_dwf_dhop(grid_dwf_t* h, int precision, const void* in, void* out, int p
   const size_t nb = subset_bytes(h, precision, subset);
   if (overlap(in, nb, out, nb)) return fail(h, GRID_DWF_ERR_ALIAS, "dhop: out overlaps in");
   if (parity == 2) {
-    const size_t hb = half_bytes(h, precision);
-    const char* ic = static_cast<const char*>(in);
-    char* oc = static_cast<char*>(out);
-    RET(dhop_half(h, precision, ic + hb, oc, 0, dag != 0, PRE_NONE, POST_NONE, 1.0, 0.0, nullptr));
-    RET(dhop_half(h, precision, ic, oc + hb, 1, dag != 0, PRE_NONE, POST_NONE, 1.0, 0.0, nullptr));
+    RET(dhop_full(h, precision, static_cast<const char*>(in), static_cast<char*>(out), dag != 0, PRE_NONE, 1.0, 0.0,
+                  nullptr));
   } else {
     RET(dhop_half(h, precision, in, out, parity, dag != 0, PRE_NONE, POST_NONE, 1.0, 0.0, nullptr));
   }
@@ -415,12 +430,9 @@ int grid_dwf_m(grid_dwf_t* h, int precision, const void* in, void* out, int dag)
   RET(check_ptr(h, out, "out"));
   const size_t nb = subset_bytes(h, precision, GRID_DWF_FULL);
   if (overlap(in, nb, out, nb)) return fail(h, GRID_DWF_ERR_ALIAS, "m: out overlaps in");
-  const size_t hb = half_bytes(h, precision);
   const char* ic = static_cast<const char*>(in);
-  char* oc = static_cast<char*>(out);
   const int pre = dag ? PRE_MOOEE_DAG : PRE_MOOEE;
-  RET(dhop_half(h, precision, ic + hb, oc, 0, dag != 0, pre, POST_NONE, -0.5, 1.0, ic));
-  RET(dhop_half(h, precision, ic, oc + hb, 1, dag != 0, pre, POST_NONE, -0.5, 1.0, ic + hb));
+  RET(dhop_full(h, precision, ic, static_cast<char*>(out), dag != 0, pre, -0.5, 1.0, ic));
   return finish(h, "m");
 }
 

@@ -18,14 +18,19 @@ static cudaError_t launch_one(const DhopArgs& a, int threads, int blocks, size_t
   if constexpr (DWF_PREC == P64) {
     kern<<<blocks, threads, smem, stream>>>(a);
   } else {
-    // full CTAs only (the packed kernel has no tail handling); a ragged end gets one more CTA
-    // flush with the end of the lattice, launched after the first so no two writes overlap in time
+    // full CTAs only (the packed kernel has no tail handling); a ragged end gets one more CTA (per
+    // half) flush with the end of the lattice, launched after the first so no two writes overlap
+    // in time. a.in2 != nullptr: both halves of a full-lattice hop in the same launches.
     const int full = a.g.N4h / a.sites_per_cta;
-    if (full > 0) kern<<<full, threads, smem, stream>>>(a);
+    const int halves = a.in2 ? 2 : 1;
+    DhopArgs m = a;
+    m.blocks1 = full;
+    if (full > 0) kern<<<halves * full, threads, smem, stream>>>(m);
     if (full * a.sites_per_cta != a.g.N4h) {
       DhopArgs t = a;
       t.site_base = a.g.N4h - a.sites_per_cta;
-      kern<<<1, threads, smem, stream>>>(t);
+      t.blocks1 = 1;
+      kern<<<halves, threads, smem, stream>>>(t);
     }
   }
   return cudaGetLastError();

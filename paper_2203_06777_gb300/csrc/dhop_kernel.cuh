@@ -47,6 +47,13 @@ struct DhopArgs {
   int sites_per_cta;  // whole sites per CTA
   int pre, post;
   int site_base;      // packed kernels: first site of block 0 (every CTA of a launch is full)
+  // Packed kernels, both halves of a full-lattice hop in one launch: CTAs from blocks1 on apply the
+  // other half (output parity 1 - out_parity, fields in2 / out2 / aux2, links swapped). A launch
+  // of one half sets blocks1 to its grid size.
+  int blocks1;
+  const void* in2;
+  void* out2;
+  const void* aux2;
   double alpha, beta;
   double d5;       // 5 - M5
   double mass;     // m
@@ -671,7 +678,10 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
   // one-CTA launch whose site_base places it flush with the end (it rewrites a few sites with the
   // same values). The kernel then has no tail handling at all: a per-thread guard around the hop
   // loop, or a clamped site index, measured 5-10% slower.
-  const int site = a.site_base + (int)blockIdx.x * a.sites_per_cta + site_local;
+  const bool second = (int)blockIdx.x >= a.blocks1;  // the other half of a full-lattice launch
+  const int bid = second ? (int)blockIdx.x - a.blocks1 : (int)blockIdx.x;
+  const int out_parity = second ? 1 - a.out_parity : a.out_parity;
+  const int site = a.site_base + bid * a.sites_per_cta + site_local;
   constexpr bool active = true;
   const size_t site_bytes = (size_t)Lsh * 2 * 24 * sizeof(T);
   const float alpha = (float)a.alpha;
@@ -686,14 +696,14 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
   constexpr int LSS = dhop_link_site_bytes(P, false);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   char* lsm = reinterpret_cast<char*>(smem_raw) + (size_t)site_local * LSS;  // [hop 8][80 bytes]
-  const char* Uo = static_cast<const char*>(a.Uout);
-  const char* Ui = static_cast<const char*>(a.Uin);
+  const char* Uo = static_cast<const char*>(second ? a.Uin : a.Uout);  // links of the output parity
+  const char* Ui = static_cast<const char*>(second ? a.Uout : a.Uin);
   // Neighbour indices and boundary phases of the eight hops, all computed before the first load
   // so that the hop loop below is straight-line code whose loads the compiler can issue early.
   int nb[8], phs[8];
   {
     int c[4];
-    cb_coords(a.g, site, a.out_parity, c);
+    cb_coords(a.g, site, out_parity, c);
 #pragma unroll
     for (int h = 0; h < 8; ++h) nb[h] = cb_neighbour(a.g, site, c, h >> 1, (h & 1) == 0, phs[h]);
     for (int h = q; h < 8; h += Lsh) {
@@ -705,7 +715,7 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
   __syncthreads();
 
   {
-    const char* in = static_cast<const char*>(a.in);
+    const char* in = static_cast<const char*>(second ? a.in2 : a.in);
 #pragma unroll
     for (int hop = 0; hop < 8; ++hop) {
       // hop = 2 mu: forward, (1 + SF gamma_mu) U_mu(x) psi(x + mu);
@@ -745,9 +755,9 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
   }
 
   // ------------------------------------------------------------ epilogue
-  char* outb = static_cast<char*>(a.out) + site_offset(site, Lsh, site_bytes);
+  char* outb = static_cast<char*>(second ? a.out2 : a.out) + site_offset(site, Lsh, site_bytes);
   if ((EK & EPI_PRE) && active && a.pre != PRE_NONE) {
-    const char* auxb = static_cast<const char*>(a.aux) + site_offset(site, Lsh, site_bytes);
+    const char* auxb = static_cast<const char*>(second ? a.aux2 : a.aux) + site_offset(site, Lsh, site_bytes);
     const float2 B = f2((float)a.beta);
     if (a.pre == PRE_AUX) {
       float2 o[24];
