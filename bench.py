@@ -193,12 +193,12 @@ def barrier(world: int):
 # ---------------------------------------------------------------- GPU arm
 
 
-def make_sets(dwf, torch, spec, prec, nsets, seed0):
+def make_sets(dwf, torch, spec, prec, nsets, seed0, fp64_arith=0):
     dims, Ls = spec["dims"], spec["Ls"]
     sets = []
     for k in range(nsets):
         U = synth.random_gauge(dims, seed=1000 * spec["case"] + seed0 + 10 * k, eps=spec["eps"])
-        op = dwf.GridDWF(dims, Ls, spec["M5"], spec["mass"], bc=BC)
+        op = dwf.GridDWF(dims, Ls, spec["M5"], spec["mass"], bc=BC, fp64_arith=fp64_arith)
         op.set_gauge(torch.from_numpy(U).cuda())
         psi = synth.random_spinor(dims, Ls, seed=1000 * spec["case"] + seed0 + 10 * k + 1)
         src = op.pack(torch.from_numpy(psi).cuda(), prec, dwf.FULL)
@@ -307,8 +307,13 @@ def run_cg(dwf, torch, spec, maxiter=20000):
                 dwf.FULL)
     out = {}
     x64 = None
-    for name, mode in (("fp64", dwf.CG_FP64), ("mixed_fp32", dwf.CG_MIXED_FP32), ("mixed_fp16", dwf.CG_MIXED_FP16),
-                       ("mixed_bf16", dwf.CG_MIXED_BF16)):
+    # *_ff: the FP64 operator applications (the whole FP64 CG; the mixed CG's true residuals) in
+    # float-float arithmetic
+    for name, mode, arith in (("fp64", dwf.CG_FP64, 0), ("mixed_fp32", dwf.CG_MIXED_FP32, 0),
+                              ("mixed_fp16", dwf.CG_MIXED_FP16, 0), ("mixed_bf16", dwf.CG_MIXED_BF16, 0),
+                              ("fp64_ff", dwf.CG_FP64, 1), ("mixed_fp32_ff", dwf.CG_MIXED_FP32, 1),
+                              ("mixed_fp16_ff", dwf.CG_MIXED_FP16, 1)):
+        op.set_fp64_arith(arith)
         torch.cuda.synchronize()
         x, st = op.cg(b, tol=1e-10, maxiter=maxiter, mode=mode, raise_on_fail=False)
         torch.cuda.synchronize()
@@ -515,11 +520,13 @@ def gpu_arm(args):
     clocks = None
     e2e = None
     wanted = args.variants.split(",")
-    for name, prec, rb in (("f32", dwf.FP32, 4), ("f64", dwf.FP64, 8), ("f16", dwf.FP16, 2), ("bf16", dwf.BF16, 2)):
+    for name, prec, rb in (("f32", dwf.FP32, 4), ("f64", dwf.FP64, 8), ("f64ff", dwf.FP64, 8), ("f16", dwf.FP16, 2),
+                           ("bf16", dwf.BF16, 2)):
         if name not in wanted:
             continue
-        sets = make_sets(dwf, torch, spec, prec, 3, seed0=0)
-        steps = args.steps if name != "f64" else max(3, args.steps // 40)
+        arith = dwf.FP64_ARITH_FLOAT_FLOAT if name == "f64ff" else dwf.FP64_ARITH_NATIVE
+        sets = make_sets(dwf, torch, spec, prec, 3, seed0=0, fp64_arith=arith)
+        steps = args.steps if name not in ("f64", "f64ff") else max(3, args.steps // (40 if name == "f64" else 10))
         if name == "f32":
             with ClockSampler(torch.cuda.current_device()) as cs:
                 secs = time_dhop(dwf, torch, sets, steps, args.warmup, world)
@@ -540,6 +547,11 @@ def gpu_arm(args):
             rec["alu_frac"] = round(gflops / (FP64_ALU_TFLOPS * 1e3), 4)
             rec["bound"] = "alu"
             rec["alu_peak_gflops"] = FP64_ALU_TFLOPS * 1e3
+        if name == "f64ff":
+            rec["arithmetic"] = "float-float (FP64 storage, pairs of FP32 numbers, ~46 significant bits)"
+            rec["bound"] = "alu (FP32 pipe)"
+            if "f64" in variants:
+                rec["speedup_vs_f64"] = round(variants["f64"]["us_per_step"] / rec["us_per_step"], 2)
         results[name] = (secs, steps, launches, per_step, gbs, gflops)
         variants[name] = rec
         if name == "f32":
@@ -646,7 +658,7 @@ def main(argv=None):
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=20)
-    ap.add_argument("--variants", default="f32,f64,f16,bf16", help="comma list of f32,f64,f16,bf16")
+    ap.add_argument("--variants", default="f32,f64,f64ff,f16,bf16", help="comma list of f32,f64,f64ff,f16,bf16")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cg", action="store_true", help="skip the CG time-to-solution comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")

@@ -92,6 +92,18 @@ int grid_dwf_create(const int dims[4], int Ls, double M5, double mass, const int
                     grid_dwf_t** out);
 int grid_dwf_destroy(grid_dwf_t* h);
 int grid_dwf_set_stream(grid_dwf_t* h, void* stream);
+
+/* Arithmetic of the GRID_DWF_FP64 hopping term (Dhop and everything built on it: M, Mpc,
+ * Mpc^+ Mpc, the FP64 CG and the FP64 true residuals of the mixed CG; storage stays FP64).
+ * GRID_DWF_FP64_ARITH_NATIVE (the default): IEEE double. GRID_DWF_FP64_ARITH_FLOAT_FLOAT: each
+ * real carried as an unevaluated sum of two floats (Dekker's double-length arithmetic: error-free
+ * TwoSum and FMA-based TwoProduct), about 46 significant bits (relative error of an operator
+ * application ~1e-14) on the FP32 pipe, which on this GPU has ~64 times the FP64 pipe's
+ * throughput. Its exponent range is float's: input magnitudes below 2^-103 read as zero and
+ * above 2^128 as infinity. Any other mode is GRID_DWF_ERR_INVALID_ARG. Applies to calls issued
+ * after it on this handle. */
+enum { GRID_DWF_FP64_ARITH_NATIVE = 0, GRID_DWF_FP64_ARITH_FLOAT_FLOAT = 1 };
+int grid_dwf_set_fp64_arith(grid_dwf_t* h, int mode);
 const char* grid_dwf_last_error(const grid_dwf_t* h);
 const char* grid_dwf_status_string(int code);
 

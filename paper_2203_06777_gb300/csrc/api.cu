@@ -35,6 +35,7 @@ struct grid_dwf {
   double* host_scal = nullptr;          // pinned mirror of scal
   std::string err;
   bool sync_debug = false;
+  int fp64_arith = GRID_DWF_FP64_ARITH_NATIVE;  // arithmetic of the FP64 hopping term
 };
 
 namespace {
@@ -182,6 +183,12 @@ int dhop_half(grid_dwf_t* h, int prec, const void* in, void* out, int out_parity
   size_t smem = dhop_link_smem_bytes(prec, a.sites_per_cta, h->c12) +
                 (post != POST_NONE ? (size_t)a.sites_per_cta * h->Ls * 24 * rbytes : 0);
   cudaError_t e;
+  if (prec == GRID_DWF_FP64 && h->fp64_arith == GRID_DWF_FP64_ARITH_FLOAT_FLOAT) {
+    smem = dhop_ff_smem_bytes(a.sites_per_cta, h->Ls, post != POST_NONE);
+    e = launch_dhop_ff(a, dag, h->c12, threads, blocks, smem, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "dhop launch (float-float)");
+    return GRID_DWF_OK;
+  }
   switch (prec) {
     case GRID_DWF_FP64: e = launch_dhop<P64>(a, dag, h->c12, threads, blocks, smem, h->stream); break;
     case GRID_DWF_FP32: e = launch_dhop<P32>(a, dag, h->c12, threads, blocks, smem, h->stream); break;
@@ -312,6 +319,14 @@ int grid_dwf_create(const int dims[4], int Ls, double M5, double mass, const int
     return e == cudaErrorMemoryAllocation ? GRID_DWF_ERR_OOM : GRID_DWF_ERR_CUDA;
   }
   *out = h;
+  return GRID_DWF_OK;
+}
+
+int grid_dwf_set_fp64_arith(grid_dwf_t* h, int mode) {
+  if (!h) return GRID_DWF_ERR_INVALID_ARG;
+  if (mode != GRID_DWF_FP64_ARITH_NATIVE && mode != GRID_DWF_FP64_ARITH_FLOAT_FLOAT)
+    return fail(h, GRID_DWF_ERR_INVALID_ARG, "fp64 arithmetic mode must be NATIVE or FLOAT_FLOAT");
+  h->fp64_arith = mode;
   return GRID_DWF_OK;
 }
 

@@ -25,6 +25,8 @@ from . import _build
 FP64, FP32, FP16, BF16 = 0, 1, 2, 3
 EVEN, ODD, FULL = 0, 1, 2
 CG_FP64, CG_MIXED_FP32, CG_MIXED_FP16, CG_MIXED_BF16 = 0, 1, 2, 3
+# arithmetic of the FP64 hopping term: IEEE double, or float-float (pairs of FP32 numbers)
+FP64_ARITH_NATIVE, FP64_ARITH_FLOAT_FLOAT = 0, 1
 
 STATUS = {
     0: "ok",
@@ -82,6 +84,7 @@ def load(build: bool = True):
             "grid_dwf_create": [ip, i, d, d, ip, i, vp, ctypes.POINTER(vp)],
             "grid_dwf_destroy": [vp],
             "grid_dwf_set_stream": [vp, vp],
+            "grid_dwf_set_fp64_arith": [vp, i],
             "grid_dwf_field_bytes": [vp, i, i, ctypes.POINTER(ctypes.c_size_t)],
             "grid_dwf_set_gauge": [vp, vp],
             "grid_dwf_pack": [vp, i, i, vp, vp],
@@ -132,7 +135,8 @@ def prec_of(t: torch.Tensor) -> int:
 class GridDWF:
     """A 5D Shamir domain-wall operator on one GPU (the handle of the C ABI)."""
 
-    def __init__(self, dims, Ls, M5=1.8, mass=0.01, bc=(1, 1, 1, -1), compress12=False, device=None):
+    def __init__(self, dims, Ls, M5=1.8, mass=0.01, bc=(1, 1, 1, -1), compress12=False, device=None,
+                 fp64_arith=FP64_ARITH_NATIVE):
         if not torch.cuda.is_available():
             raise RuntimeError("GridDWF needs a CUDA device; there is no CPU fallback")
         self.lib = load()
@@ -154,6 +158,9 @@ class GridDWF:
         if rc != 0:
             raise GridDWFError(rc, "grid_dwf_create rejected the parameters")
         self._h = h
+        self.fp64_arith = FP64_ARITH_NATIVE
+        if fp64_arith != FP64_ARITH_NATIVE:
+            self.set_fp64_arith(fp64_arith)
 
     # -------------------------------------------------------------- plumbing
     def close(self):
@@ -173,6 +180,14 @@ class GridDWF:
         if rc != 0:
             raise GridDWFError(rc, f"{name}: {self.lib.grid_dwf_last_error(self._h).decode()}")
         return rc
+
+    def set_fp64_arith(self, mode: int):
+        """Arithmetic of every FP64 hopping-term application on this handle (grid_dwf_set_fp64_arith):
+        FP64_ARITH_NATIVE (IEEE double) or FP64_ARITH_FLOAT_FLOAT (float-float, ~46 bits)."""
+        rc = self.lib.grid_dwf_set_fp64_arith(self._h, int(mode))
+        if rc != 0:
+            raise GridDWFError(rc, f"grid_dwf_set_fp64_arith: {self.lib.grid_dwf_last_error(self._h).decode()}")
+        self.fp64_arith = int(mode)
 
     def _subset_of(self, t: torch.Tensor) -> int:
         if t.numel() == self.half_reals:
