@@ -82,7 +82,7 @@ typedef struct {
 } grid_dwf_cg_stats;
 
 /* Create an operator on an Lx x Ly x Lz x Lt x Ls lattice.
- * dims[4] = {Lx, Ly, Lz, Lt}, each even and >= 2, Lx*Ly*Lz*Lt/2 < 2^31 / 8; 1 <= Ls <= 256;
+ * dims[4] = {Lx, Ly, Lz, Lt}, each even and >= 2, Lx*Ly*Lz*Lt/2 < 2^31 / 8; 1 <= Ls <= 128;
  * M5, mass finite, and Mooee invertible for them; bc[4] each +1 (periodic) or -1
  * (antiperiodic), NULL meaning {+1, +1, +1, -1}; compress12 != 0 stores links as two rows (the
  * third rebuilt as the conjugated cross product, exact for SU(3) links); stream is a

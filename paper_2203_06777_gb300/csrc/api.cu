@@ -270,7 +270,7 @@ int grid_dwf_create(const int dims[4], int Ls, double M5, double mass, const int
     if (dims[m] < 2 || dims[m] % 2) return GRID_DWF_ERR_INVALID_ARG;
     V *= dims[m];
   }
-  if (Ls < 1 || Ls > 256) return GRID_DWF_ERR_INVALID_ARG;
+  if (Ls < 1 || Ls > 128) return GRID_DWF_ERR_INVALID_ARG;  // FP64: one thread per slice, 128 per CTA
   if ((V / 2) * 8 >= (1L << 31)) return GRID_DWF_ERR_INVALID_ARG;
   if (!std::isfinite(M5) || !std::isfinite(mass)) return GRID_DWF_ERR_INVALID_ARG;
   const int defbc[4] = {1, 1, 1, -1};

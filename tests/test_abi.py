@@ -56,7 +56,7 @@ def test_invalid_create_rejected_before_any_device_work(lib):
     assert f(dims(4, 4, 4, 3), 8, 1.8, 0.01, bc, 0, None, ctypes.byref(h)) == -1
     assert f(dims(4, 4, 4, 0), 8, 1.8, 0.01, bc, 0, None, ctypes.byref(h)) == -1
     assert f(dims(4, 4, 4, 4), 0, 1.8, 0.01, bc, 0, None, ctypes.byref(h)) == -1
-    assert f(dims(4, 4, 4, 4), 257, 1.8, 0.01, bc, 0, None, ctypes.byref(h)) == -1
+    assert f(dims(4, 4, 4, 4), 129, 1.8, 0.01, bc, 0, None, ctypes.byref(h)) == -1
     assert f(dims(4, 4, 4, 4), 8, float("nan"), 0.01, bc, 0, None, ctypes.byref(h)) == -1
     assert f(dims(4, 4, 4, 4), 8, 5.0, 0.01, bc, 0, None, ctypes.byref(h)) == -1  # 5 - M5 = 0
     assert f(dims(4, 4, 4, 4), 8, 1.8, 0.01, (ctypes.c_int * 4)(1, 1, 1, 2), 0, None, ctypes.byref(h)) == -1
