@@ -372,10 +372,21 @@ def run_force(dwf, torch, spec, reps=20):
     e1.record()
     torch.cuda.synchronize()
     ms64 = e0.elapsed_time(e1) / max(2, reps // 4)
+    # FP64 fields with the float-float arithmetic (M psi and the force kernel)
+    op.set_fp64_arith(dwf.FP64_ARITH_FLOAT_FLOAT)
+    op.force(f64, chi=chi64)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        rc = op.lib.grid_dwf_force(op._h, dwf.FP64, dwf._ptr(f64), dwf._ptr(chi64), dwf._ptr(F), dwf._ptr(G), None)
+        assert rc == 0
+    e1.record()
+    torch.cuda.synchronize()
+    ms64ff = e0.elapsed_time(e1) / reps
     op.close()
     return {"workload": "dwf_16x16x16x16_ls16_haar", "ms_per_force": round(ms, 4), "reps": reps,
             "precision": "fp32 fields, fp64 accumulation across blocks of 8 slice pairs",
-            "ms_per_force_fp64": round(ms64, 4),
+            "ms_per_force_fp64": round(ms64, 4), "ms_per_force_fp64_float_float": round(ms64ff, 4),
             "includes": "M psi (one launch: Dhop with the fused Mooee term, both halves), |M psi|^2, force and ambient-gradient kernel"}
 
 

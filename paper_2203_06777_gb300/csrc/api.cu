@@ -14,7 +14,7 @@
 
 namespace gdwf {
 cudaError_t launch_force(int prec, bool c12, const Geom& g, const void* psi, const void* chi, const void* Ue,
-                         const void* Uo, double* F, double* G, double coef, cudaStream_t st);
+                         const void* Uo, double* F, double* G, double coef, bool float_float, cudaStream_t st);
 }
 
 using namespace gdwf;
@@ -742,7 +742,7 @@ int grid_dwf_force(grid_dwf_t* h, int precision, const void* psi, void* chi, dou
      "force action");
   RET(ensure_gauge(h, precision));
   if (F || G)
-    CK(launch_force(precision, h->c12, h->g, psi, c, h->gauge[precision][0], h->gauge[precision][1], F, G, 1.0,
+    CK(launch_force(precision, h->c12, h->g, psi, c, h->gauge[precision][0], h->gauge[precision][1], F, G, 1.0, h->fp64_arith == GRID_DWF_FP64_ARITH_FLOAT_FLOAT,
                     h->stream),
        "force");
   RET(read_scalars(h));
@@ -799,7 +799,7 @@ int grid_dwf_pf_force(grid_dwf_t* h, const void* phi, void* X, double tol, int m
       b = b32;
     }
     RET(ensure_gauge(h, precision));
-    CK(launch_force(precision, h->c12, h->g, a, b, h->gauge[precision][0], h->gauge[precision][1], F, G, -0.5,
+    CK(launch_force(precision, h->c12, h->g, a, b, h->gauge[precision][0], h->gauge[precision][1], F, G, -0.5, h->fp64_arith == GRID_DWF_FP64_ARITH_FLOAT_FLOAT,
                     h->stream),
        "pf_force force");
   }

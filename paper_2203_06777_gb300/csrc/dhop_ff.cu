@@ -16,172 +16,25 @@
 // Same operator, layout, thread mapping (one thread per (site, slice)), link staging and fused
 // epilogues (out = post(alpha Dhop in + beta pre(aux))) as the FP64 kernel; see there.
 #include "dhop_kernel.cuh"
+#include "ff_arith.cuh"
 
 namespace gdwf {
 namespace {
 
-struct ff {
-  float hi, lo;
-};
+using namespace ffa;
 
-__device__ __forceinline__ ff ff_make(float hi, float lo) {
-  ff r;
-  r.hi = hi;
-  r.lo = lo;
-  return r;
-}
-
-// s + e == a + b exactly, for any a, b (Knuth's TwoSum, six additions).
-__device__ __forceinline__ float two_sum(float a, float b, float& e) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return s;
-}
-
-// Renormalise hi + lo with |hi| >= |lo| (Dekker's FastTwoSum, three additions).
-__device__ __forceinline__ ff fast_two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  return ff_make(s, __fsub_rn(b, __fsub_rn(s, a)));
-}
-
-__device__ __forceinline__ ff ff_neg(ff a) { return ff_make(-a.hi, -a.lo); }
-
-// a + SG b (SG = +1 or -1 at compile time): TwoSum of the leading parts, the trailing parts added
-// to its error, one renormalisation (eleven instructions).
-template <int SG>
-__device__ __forceinline__ ff ff_add(ff a, ff b) {
-  const float bh = SG > 0 ? b.hi : -b.hi, bl = SG > 0 ? b.lo : -b.lo;
-  float e;
-  const float s = two_sum(a.hi, bh, e);
-  e = __fadd_rn(e, __fadd_rn(a.lo, bl));
-  return fast_two_sum(s, e);
-}
-
-// a * b: TwoProduct of the leading parts plus the two cross terms (seven instructions).
-__device__ __forceinline__ ff ff_mul(ff a, ff b) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  float e = __fmaf_rn(a.hi, b.hi, -p);
-  e = __fmaf_rn(a.hi, b.lo, e);
-  e = __fmaf_rn(a.lo, b.hi, e);
-  return fast_two_sum(p, e);
-}
-
-// Dot-product accumulator S + E: the products' leading parts are summed with TwoSum into S, all
-// rounding errors and cross terms in FP32 into E, and S + E is renormalised once at the end.
-struct ffacc {
-  float s, e;
-};
-
-__device__ __forceinline__ void dot_first(ffacc& A, ff a, ff b, bool neg) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  float e = __fmaf_rn(a.hi, b.hi, -p);
-  e = __fmaf_rn(a.hi, b.lo, e);
-  e = __fmaf_rn(a.lo, b.hi, e);
-  A.s = neg ? -p : p;
-  A.e = neg ? -e : e;
-}
-
-// A += SG a b (twelve instructions).
-template <int SG>
-__device__ __forceinline__ void dot_add(ffacc& A, ff a, ff b) {
-  const float ah = SG > 0 ? a.hi : -a.hi, al = SG > 0 ? a.lo : -a.lo;
-  const float p = __fmul_rn(ah, b.hi);
-  float e = __fmaf_rn(ah, b.hi, -p);
-  e = __fmaf_rn(ah, b.lo, e);
-  e = __fmaf_rn(al, b.hi, e);
-  float t;
-  A.s = two_sum(A.s, p, t);
-  A.e = __fadd_rn(A.e, __fadd_rn(t, e));
-}
-
-__device__ __forceinline__ ff dot_result(const ffacc& A) { return fast_two_sum(A.s, A.e); }
-
-// FP64 -> float-float with integer operations only (conversions through the FP64 pipe would cost
-// as much as the FP64 arithmetic this kernel avoids). hi takes the sign, the exponent and the
-// leading 23 stored mantissa bits (truncated); lo the next 23 bits, formed as (1.f x 2^k) - 2^k,
-// which is exact. Values of magnitude below 2^-103 give 0; above FP32's range, infinity.
-__device__ __forceinline__ ff ff_from_double(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const uint32_t H = (uint32_t)(b >> 32), L = (uint32_t)b;
-  const uint32_t sgn = H & 0x80000000u;
-  const uint32_t mag = H & 0x7FFFFFFFu;  // exponent and leading 20 mantissa bits
-  // mantissa bits 51..29 below a 9-bit window of the exponent; adding 2^30 rebiases that window
-  // from FP64 (1023) to FP32 (127) for every exponent in FP32's normal range
-  const uint32_t hb = __funnelshift_l(L, H, 3) + 0x40000000u;  // bit 31 clear when in range
-  const uint32_t pe = (hb & 0x7F800000u) - (23u << 23);  // 2^k with k = exponent(hi) - 23
-  const float lo = __fsub_rn(__uint_as_float(sgn | pe | ((L >> 6) & 0x7FFFFFu)), __uint_as_float(sgn | pe));
-  // exponent of x in [920, 1150] (FP64 bias): both parts exact as above
-  const bool in_range = mag - (920u << 20) < ((1151u - 920u) << 20);
-  const bool big = mag >= (1151u << 20);
-  const uint32_t hi_bits = in_range ? (sgn | hb) : (big ? (sgn | 0x7F800000u) : sgn);
-  return ff_make(__uint_as_float(hi_bits), in_range ? lo : 0.f);
-}
-
-// FP32 -> FP64 with integer operations (exact; FP32 subnormals read as zero).
-__device__ __forceinline__ double widen(float f) {
-  const uint32_t b = __float_as_uint(f);
-  const uint32_t sgn = b & 0x80000000u;
-  const uint32_t e = (b >> 23) & 0xFFu;
-  const uint32_t hb = sgn | ((e + 896u) << 20) | ((b >> 3) & 0xFFFFFu);
-  const uint32_t H = e == 0 ? sgn : (e == 255 ? (sgn | 0x7FF00000u | ((b & 0x7FFFFFu) ? 0x80000u : 0u)) : hb);
-  const uint32_t L = (e == 0 || e == 255) ? 0u : (b << 29);
-  return __hiloint2double((int)H, (int)L);
-}
-
-// The value hi + lo rounded to FP64 (one FP64 addition).
-__device__ __forceinline__ double ff_to_double(ff v) { return widen(v.hi) + widen(v.lo); }
-
-__device__ __forceinline__ ff ff_const(double x) { return ff_from_double(x); }
-
-// ---------------------------------------------------------------- spin algebra in float-float
-// Same conventions as project / su3_mul / accumulate of dhop_kernel.cuh (chiral basis; SIG = +1
-// applies 1 + gamma_mu). The loops over hops and colour rows below are not unrolled: unrolled,
-// the float-float arithmetic of eight hops is about 300 KB of machine code, far more than the
-// SM's instruction caches, and the warps stalled on instruction fetch. So every hop runs the same
-// short code: the projection is h_k = psi_k + w_k psi_{p_k} (k = 0, 1; w_k in {+-1, +-i}, p_k in
-// {2, 3}), with the lower spins loaded at hop-dependent addresses and their signs flipped on
-// load (its additions run in FP64: the stored reals are FP64 anyway); the link is staged as U or U^+ so that the colour product has one form; the product is
-// written to a per-thread shared-memory slot, from which the reconstruction of the lower spins
-// reads at hop-dependent addresses, acc_{2+j} += w'_j uh_{q_j}.
-
-// Multiplication by w in {+1, -1, +i, -i} (codes 0..3; code ^ 1 negates w): w (x + iy) takes
-// its real part from x or y (swap) and flips the sign of either part.
-struct WMul {
-  bool swap;
-  uint32_t nr, ni;  // 0x80000000 where the real / imaginary part is negated
-};
-
-__device__ __forceinline__ WMul wmul(int code) {
-  WMul w;
-  w.swap = code >= 2;                                        // +i: (-y, x), -i: (y, -x)
-  w.nr = (code == 1 || code == 2) ? 0x80000000u : 0u;
-  w.ni = (code == 1 || code == 3) ? 0x80000000u : 0u;
-  return w;
-}
-
-// Codes of w per (mu, k), two bits each at bit 4 mu + 2 k, for projector sign S = +1 (S = -1: ^ 1).
-constexpr uint32_t pack_w(int a0, int a1, int b0, int b1, int c0, int c1, int d0, int d1) {
-  return (uint32_t)(a0 | a1 << 2 | b0 << 4 | b1 << 6 | c0 << 8 | c1 << 10 | d0 << 12 | d1 << 14);
-}
-// projection h_k = psi_k + w_k psi_{p_k}, p = (3, 2) for mu < 2, else (2, 3):
-//   mu = 0: (-i, -i); 1: (-1, +1); 2: (-i, +i); 3: (+1, +1)
-constexpr uint32_t PROJ_W = pack_w(3, 3, 1, 0, 3, 2, 0, 0);
-// reconstruction of the lower spins, acc[2 + j] += w'_j uh_{q_j}, q = (1, 0) for mu < 2, else (0, 1):
-//   mu = 0: (+i, +i); 1: (+1, -1); 2: (+i, -i); 3: (+1, +1)
-constexpr uint32_t RECON_W = pack_w(2, 2, 0, 1, 2, 3, 0, 0);
-
-__device__ __forceinline__ int w_code(uint32_t table, int mu, int k, int S) {
-  return (int)((table >> (4 * mu + 2 * k)) & 3u) ^ (S < 0 ? 1 : 0);
-}
-
-__device__ __forceinline__ ff flip(ff v, uint32_t n) {
-  return ff_make(__uint_as_float(__float_as_uint(v.hi) ^ n), __uint_as_float(__float_as_uint(v.lo) ^ n));
-}
+// ---------------------------------------------------------------- the hop loop's code shape
+// The loops over hops and colour rows below are not unrolled: unrolled, the float-float
+// arithmetic of eight hops is about 300 KB of machine code, far more than the SM's instruction
+// caches, and the warps stalled on instruction fetch. So every hop runs the same short code: the
+// lower spins of the projection are loaded at hop-dependent addresses with their signs flipped on
+// load (the projection's additions run in FP64: the stored reals are FP64 anyway); the link is
+// staged as U or U^+ so that the colour product has one form; the product is written to a
+// per-thread shared-memory slot, from which the reconstruction of the lower spins reads at
+// hop-dependent addresses.
 
 // Row a of o = U h for both spins: u the row's 3 complex entries (6 ff), h the half spinor.
-// Each output real is a six-term dot product accumulated exactly up to its final
-// renormalisation.
+// Each output real is a six-term dot product, returned as its unnormalised pair (S, E).
 __device__ __forceinline__ void su3_row_ff(const ff* u, const ff* h, ff* o /* [sp][re, im] */) {
 #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
@@ -201,8 +54,8 @@ __device__ __forceinline__ void su3_row_ff(const ff* u, const ff* h, ff* o /* [s
       dot_add<-1>(re, ui, hi);
       dot_add<+1>(im, ui, hr);
     }
-    o[sp * 2] = dot_result(re);
-    o[sp * 2 + 1] = dot_result(im);
+    o[sp * 2] = ff_make(re.s, re.e);  // unnormalised: only ever added into an accumulator
+    o[sp * 2 + 1] = ff_make(im.s, im.e);
   }
 }
 
@@ -266,12 +119,6 @@ __device__ __forceinline__ void stage_link_ff(ff* dst, const char* src, bool neg
       dst[(a * 3 + b) * 2] = re;
       dst[(a * 3 + b) * 2 + 1] = im;
     }
-}
-
-// One real of an FP64 field with its sign bit flipped by `neg` (0 or 0x80000000).
-__device__ __forceinline__ double ld64(const char* p, uint32_t neg) {
-  const double d = __ldg(reinterpret_cast<const double*>(p));
-  return __hiloint2double(__double2hiint(d) ^ (int)neg, __double2loint(d));
 }
 
 // In-place inverse of the fifth-dimension matrix along one real of one site (stride 24 between
@@ -361,25 +208,8 @@ __global__ void __launch_bounds__(128, DWF_FF_MIN_BLOCKS) dhop_kernel_ff(const _
       const int mu = hop >> 1;
       const int S = (hop & 1) == 0 ? SF : SB;
       const char* blk = in + site_offset(nbs[hop], Lsh, site_bytes);
-      // h_k = psi_k + w_k psi_{p_k}: the upper spins as stored; for the lower spin p_k the real
-      // slot reads its imaginary part when w_k is imaginary (and the other way round), with signs
-      const WMul w0 = wmul(w_code(PROJ_W, mu, 0, S)), w1 = wmul(w_code(PROJ_W, mu, 1, S));
-      const int p0 = mu < 2 ? 3 : 2, p1 = 5 - p0;
-      const char* l0 = blk + (size_t)(p0 * 6 + (w0.swap ? 1 : 0)) * cs;
-      const char* l1 = blk + (size_t)(p1 * 6 + (w1.swap ? 1 : 0)) * cs;
-      const ptrdiff_t o0 = w0.swap ? -(ptrdiff_t)cs : (ptrdiff_t)cs;
-      const ptrdiff_t o1 = w1.swap ? -(ptrdiff_t)cs : (ptrdiff_t)cs;
-      // the projection's additions in FP64 (one instruction each on the otherwise idle FP64 pipe,
-      // against two conversions and a float-float addition), then one conversion per real
       ff h[12];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const size_t cc = (size_t)(2 * c) * cs;
-        h[(0 * 3 + c) * 2] = ff_from_double(ld64(blk + cc, 0u) + ld64(l0 + cc, w0.nr));
-        h[(0 * 3 + c) * 2 + 1] = ff_from_double(ld64(blk + cc + cs, 0u) + ld64(l0 + cc + o0, w0.ni));
-        h[(1 * 3 + c) * 2] = ff_from_double(ld64(blk + 6 * cs + cc, 0u) + ld64(l1 + cc, w1.nr));
-        h[(1 * 3 + c) * 2 + 1] = ff_from_double(ld64(blk + 7 * cs + cc, 0u) + ld64(l1 + cc + o1, w1.ni));
-      }
+      project_load_ff(blk, mu, S, cs, h);
       // uh = U h (U^+ h on backward hops), row by row into this thread's slots uhs[r * bd]
 #pragma unroll 1
       for (int ra = 0; ra < 3; ++ra) {
@@ -394,7 +224,7 @@ __global__ void __launch_bounds__(128, DWF_FF_MIN_BLOCKS) dhop_kernel_ff(const _
       }
       // upper spins: acc += uh; lower spins: acc_{2+j} += w'_j uh_{q_j}
 #pragma unroll
-      for (int r = 0; r < 12; ++r) acc[r] = ff_add<+1>(acc[r], uhs[r * bd]);
+      for (int r = 0; r < 12; ++r) acc_add(acc[r], uhs[r * bd]);
       const WMul v0 = wmul(w_code(RECON_W, mu, 0, S)), v1 = wmul(w_code(RECON_W, mu, 1, S));
       const int q0 = mu < 2 ? 1 : 0, q1 = 1 - q0;
       const ff* s0 = uhs + (q0 * 6 + (v0.swap ? 1 : 0)) * bd;
@@ -402,12 +232,14 @@ __global__ void __launch_bounds__(128, DWF_FF_MIN_BLOCKS) dhop_kernel_ff(const _
       const int d0 = v0.swap ? -bd : bd, d1 = v1.swap ? -bd : bd;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        acc[(2 * 3 + c) * 2] = ff_add<+1>(acc[(2 * 3 + c) * 2], flip(s0[2 * c * bd], v0.nr));
-        acc[(2 * 3 + c) * 2 + 1] = ff_add<+1>(acc[(2 * 3 + c) * 2 + 1], flip(s0[2 * c * bd + d0], v0.ni));
-        acc[(3 * 3 + c) * 2] = ff_add<+1>(acc[(3 * 3 + c) * 2], flip(s1[2 * c * bd], v1.nr));
-        acc[(3 * 3 + c) * 2 + 1] = ff_add<+1>(acc[(3 * 3 + c) * 2 + 1], flip(s1[2 * c * bd + d1], v1.ni));
+        acc_add(acc[(2 * 3 + c) * 2], flip(s0[2 * c * bd], v0.nr));
+        acc_add(acc[(2 * 3 + c) * 2 + 1], flip(s0[2 * c * bd + d0], v0.ni));
+        acc_add(acc[(3 * 3 + c) * 2], flip(s1[2 * c * bd], v1.nr));
+        acc_add(acc[(3 * 3 + c) * 2 + 1], flip(s1[2 * c * bd + d1], v1.ni));
       }
     }
+#pragma unroll
+    for (int r = 0; r < 24; ++r) acc[r] = fast_two_sum(acc[r].hi, acc[r].lo);
     if (a.alpha != 1.0) {
       const ff al = ff_const(a.alpha);
 #pragma unroll

@@ -27,6 +27,7 @@
 #include <type_traits>
 
 #include "dhop_kernel.cuh"
+#include "ff_arith.cuh"
 
 namespace gdwf {
 
@@ -44,6 +45,70 @@ constexpr int FORCE_PART_STRIDE = 37;
 inline size_t force_smem_per_site(int prec, int nsg) {
   const size_t v = prec == P64 ? sizeof(double) : sizeof(float);
   return (size_t)nsg * FORCE_PART_STRIDE * v + (36 + 18 + 18) * v + 2 * sizeof(long);
+}
+
+// The per-site steps after the slice sums B1, B2 (bsum) of direction mu are in shared memory:
+// each site's link, then one (site, a, b) entry per task:
+//   G[a][b] = -phase (conj(B1[b][a]) + B2[a][b]),  Y = phase (-U B1 + B2 U^+),
+// then F = -TA(Y), TA(Y)[a][b] = (Y[a][b] - conj(Y[b][a]))/2 - delta_ab tr(Y - Y^+)/6.
+// A: the arithmetic of the link algebra (double for FP64 fields, float for FP32 fields).
+template <int P, bool C12, typename A>
+__device__ __forceinline__ void force_site_algebra(int mu, int p, int first, int nsites, const char* Ue, const char* Uo,
+                                                   const A* bsum, A* usm, A* ysm, const long* lex_sm,
+                                                   const int* ph_sm, double coef, double* F, double* G) {
+  using R = typename Store<P>::R;
+  constexpr int LB = link_bytes(sizeof(typename Store<P>::T), C12);
+  const int tid = threadIdx.x;
+  for (int sl = tid; sl < nsites; sl += blockDim.x) {  // the link U_mu(x), third row rebuilt if stored as 12 reals
+    R ur[18];
+    load_link<P, C12>((p ? Uo : Ue) + ((size_t)(first + sl) * 4 + mu) * LB, ur);
+#pragma unroll
+    for (int k = 0; k < 18; ++k) usm[(size_t)sl * 18 + k] = (A)ur[k];
+  }
+  __syncthreads();
+  // ---- link algebra, one (site, a, b) entry per task:
+  //   G[a][b] = -phase (conj(B1[b][a]) + B2[a][b]),  Y = phase (-U B1 + B2 U^+)
+  for (int task = tid; task < nsites * 9; task += blockDim.x) {
+    const int sl = task / 9, ab = task - sl * 9, a = ab / 3, b = ab - a * 3;
+    const A phd = (A)(coef * (double)ph_sm[sl]);  // F and G are linear in the boundary phase and coef
+    const A* B1 = bsum + (size_t)sl * 36;
+    const A* B2 = B1 + 18;
+    const A* ur = usm + (size_t)sl * 18;
+    A yr = 0, yi = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const A ar = ur[(a * 3 + k) * 2], ai = ur[(a * 3 + k) * 2 + 1];
+      const A br = B1[(k * 3 + b) * 2], bi = B1[(k * 3 + b) * 2 + 1];
+      yr -= ar * br - ai * bi;
+      yi -= ar * bi + ai * br;
+      const A cr = B2[(a * 3 + k) * 2], ci = B2[(a * 3 + k) * 2 + 1];
+      const A dr = ur[(b * 3 + k) * 2], di = -ur[(b * 3 + k) * 2 + 1];  // (U^+)[k][b] = conj(U[b][k])
+      yr += cr * dr - ci * di;
+      yi += cr * di + ci * dr;
+    }
+    ysm[(size_t)sl * 18 + ab * 2] = phd * yr;
+    ysm[(size_t)sl * 18 + ab * 2 + 1] = phd * yi;
+    if (G) {
+      double* Go = G + (lex_sm[sl] * 4 + mu) * 18;
+      Go[ab * 2] = (double)(-phd * (B1[(b * 3 + a) * 2] + B2[ab * 2]));
+      Go[ab * 2 + 1] = (double)(-phd * (-B1[(b * 3 + a) * 2 + 1] + B2[ab * 2 + 1]));
+    }
+  }
+  __syncthreads();
+  // ---- F = -TA(Y): TA(Y)[a][b] = (Y[a][b] - conj(Y[b][a]))/2 - delta_ab tr(Y - Y^+)/6
+  if (F) {
+    for (int task = tid; task < nsites * 9; task += blockDim.x) {
+      const int sl = task / 9, ab = task - sl * 9, a = ab / 3, b = ab - a * 3;
+      const A* Y = ysm + (size_t)sl * 18;
+      const A trim = Y[1] + Y[9] + Y[17];  // Im tr Y; tr(Y - Y^+) = 2 i Im tr Y
+      const A tr_ = (A)0.5 * (Y[(a * 3 + b) * 2] - Y[(b * 3 + a) * 2]);
+      A ti_ = (A)0.5 * (Y[(a * 3 + b) * 2 + 1] + Y[(b * 3 + a) * 2 + 1]);
+      if (a == b) ti_ -= trim / (A)3;
+      double* Fo = F + (lex_sm[sl] * 4 + mu) * 18;
+      Fo[ab * 2] = -(double)tr_;
+      Fo[ab * 2 + 1] = -(double)ti_;
+    }
+  }
 }
 
 template <int P, bool C12>
@@ -172,62 +237,108 @@ __global__ void __launch_bounds__(128) k_force(const Geom g, const char* psi, co
       }
       bsum[(size_t)sl * 36 + e] = total;
     }
-    for (int sl = tid; sl < nsites; sl += blockDim.x) {  // the link U_mu(x), third row rebuilt if stored as 12 reals
-      R ur[18];
-      load_link<P, C12>((p ? Uo : Ue) + ((size_t)(first + sl) * 4 + mu) * LB, ur);
+    force_site_algebra<P, C12, A>(mu, p, first, nsites, Ue, Uo, bsum, usm, ysm, lex_sm, ph_sm, coef, F, G);
+    __syncthreads();  // shared memory is reused by the next direction
+  }
+}
+
+// FP64 fields in float-float arithmetic (the handle's FP64 arithmetic set to float-float): the
+// per-slice products in pairs of FP32 numbers, the slice sums in float-float, then the site's
+// sums rounded to FP64 for the (per 4D site, cheap) link algebra. One thread per (site, slice)
+// (Ls <= 128, so one slice each); the direction loop is not unrolled, and the projections read
+// their direction-dependent parts by address, so that one short code path serves every mu (the
+// unrolled float-float code would overflow the instruction cache, as in the hopping kernel).
+template <bool C12>
+__global__ void __launch_bounds__(128) k_force_ff(const Geom g, const char* psi, const char* chi, const char* Ue,
+                                                  const char* Uo, double* F, double* G, double coef, int nsg,
+                                                  int spc) {
+  using namespace ffa;
+  const int Lsh = ls_half(g.Ls);
+  const size_t site_bytes = (size_t)Lsh * 2 * 24 * 8;
+  const size_t half_bytes = (size_t)g.N4h * site_bytes;
+  const size_t cs = chunk_stride(Lsh);
+  const int p = blockIdx.x & 1;
+  const int first = (blockIdx.x >> 1) * spc;
+  const int tid = threadIdx.x;
+  const int site_local = tid / nsg;
+  const int t = tid - site_local * nsg;  // the thread's slice
+  const int nsites = min(spc, g.N4h - first);
+  const bool active = site_local < nsites;
+  const int i = first + (active ? site_local : 0);
+  int c[4];
+  cb_coords(g, i, p, c);
+  const char* psi_x = psi + p * half_bytes + site_offset(i, Lsh, site_bytes) + (size_t)t * 8;
+  const char* chi_x = chi + p * half_bytes + site_offset(i, Lsh, site_bytes) + (size_t)t * 8;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  long* lex_sm = reinterpret_cast<long*>(smem_raw);
+  int* ph_sm = reinterpret_cast<int*>(lex_sm + spc);
+  ff* part = reinterpret_cast<ff*>(smem_raw + (size_t)spc * 2 * sizeof(long));  // [spc][nsg][37] (S, E) pairs
+  double* bsum = reinterpret_cast<double*>(part + (size_t)spc * nsg * FORCE_PART_STRIDE);  // [spc][36]
+  double* usm = bsum + (size_t)spc * 36;
+  double* ysm = usm + (size_t)spc * 18;
+  if (active && t == 0) lex_sm[site_local] = c[0] + (long)g.L[0] * (c[1] + (long)g.L[1] * (c[2] + (long)g.L[2] * c[3]));
+  // forward neighbours and phases at compile-time mu (a runtime mu would index c and g through
+  // local memory), picked by selects in the rolled loop below
+  int nf[4], pf[4];
 #pragma unroll
-      for (int k = 0; k < 18; ++k) usm[(size_t)sl * 18 + k] = (A)ur[k];
+  for (int m = 0; m < 4; ++m) nf[m] = cb_neighbour(g, i, c, m, true, pf[m]);
+
+#pragma unroll 1
+  for (int mu = 0; mu < 4; ++mu) {
+    if (active) {
+      const int j = mu == 0 ? nf[0] : mu == 1 ? nf[1] : mu == 2 ? nf[2] : nf[3];
+      const int ph = mu == 0 ? pf[0] : mu == 1 ? pf[1] : mu == 2 ? pf[2] : pf[3];
+      if (t == 0) ph_sm[site_local] = ph;
+      const size_t jo = (1 - p) * half_bytes + site_offset(j, Lsh, site_bytes) + (size_t)t * 8;
+      ff* dst = part + ((size_t)site_local * nsg + t) * FORCE_PART_STRIDE;
+      // term 0: B1 = psi(x+mu) (x) [(1 - gamma) chi(x)]^+;  term 1: B2 = psi(x) (x) [(1 + gamma) chi(x+mu)]^+
+#pragma unroll 1
+      for (int term = 0; term < 2; ++term) {
+        const int S = term == 0 ? -1 : +1;
+        ff ha[12], hb[12];
+        project_load_ff(term == 0 ? psi + jo : psi_x, mu, S, cs, ha);
+        project_load_ff(term == 0 ? chi_x : chi + jo, mu, S, cs, hb);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {  // sum_h ha[h][a] conj(hb[h][b])
+            ffacc re, im;
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+              const ff xr = ha[(hh * 3 + a) * 2], xi = ha[(hh * 3 + a) * 2 + 1];
+              const ff yr = hb[(hh * 3 + b) * 2], yi = hb[(hh * 3 + b) * 2 + 1];
+              if (hh == 0) {
+                dot_first(re, xr, yr, false);
+                dot_first(im, xi, yr, false);
+              } else {
+                dot_add<+1>(re, xr, yr);
+                dot_add<+1>(im, xi, yr);
+              }
+              dot_add<+1>(re, xi, yi);
+              dot_add<-1>(im, xr, yi);
+            }
+            dst[term * 18 + (a * 3 + b) * 2] = ff_make(re.s, re.e);
+            dst[term * 18 + (a * 3 + b) * 2 + 1] = ff_make(im.s, im.e);
+          }
+      }
     }
     __syncthreads();
-    // ---- link algebra, one (site, a, b) entry per task:
-    //   G[a][b] = -phase (conj(B1[b][a]) + B2[a][b]),  Y = phase (-U B1 + B2 U^+)
-    for (int task = tid; task < nsites * 9; task += blockDim.x) {
-      const int sl = task / 9, ab = task - sl * 9, a = ab / 3, b = ab - a * 3;
-      const A phd = (A)(coef * (double)ph_sm[sl]);  // F and G are linear in the boundary phase and coef
-      const A* B1 = bsum + (size_t)sl * 36;
-      const A* B2 = B1 + 18;
-      const A* ur = usm + (size_t)sl * 18;
-      A yr = 0, yi = 0;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const A ar = ur[(a * 3 + k) * 2], ai = ur[(a * 3 + k) * 2 + 1];
-        const A br = B1[(k * 3 + b) * 2], bi = B1[(k * 3 + b) * 2 + 1];
-        yr -= ar * br - ai * bi;
-        yi -= ar * bi + ai * br;
-        const A cr = B2[(a * 3 + k) * 2], ci = B2[(a * 3 + k) * 2 + 1];
-        const A dr = ur[(b * 3 + k) * 2], di = -ur[(b * 3 + k) * 2 + 1];  // (U^+)[k][b] = conj(U[b][k])
-        yr += cr * dr - ci * di;
-        yi += cr * di + ci * dr;
-      }
-      ysm[(size_t)sl * 18 + ab * 2] = phd * yr;
-      ysm[(size_t)sl * 18 + ab * 2 + 1] = phd * yi;
-      if (G) {
-        double* Go = G + (lex_sm[sl] * 4 + mu) * 18;
-        Go[ab * 2] = (double)(-phd * (B1[(b * 3 + a) * 2] + B2[ab * 2]));
-        Go[ab * 2 + 1] = (double)(-phd * (-B1[(b * 3 + a) * 2 + 1] + B2[ab * 2 + 1]));
-      }
+    // ---- sum over the site's slices in float-float, one (site, entry) per task, rounded to FP64
+    for (int task = tid; task < nsites * 36; task += blockDim.x) {
+      const int sl = task / 36, e = task - sl * 36;
+      const ff* src = part + (size_t)sl * nsg * FORCE_PART_STRIDE + e;
+      ff total = ff_make(0.f, 0.f);
+      for (int k = 0; k < nsg; ++k) acc_add(total, src[(size_t)k * FORCE_PART_STRIDE]);
+      bsum[(size_t)sl * 36 + e] = ff_to_double(fast_two_sum(total.hi, total.lo));
     }
-    __syncthreads();
-    // ---- F = -TA(Y): TA(Y)[a][b] = (Y[a][b] - conj(Y[b][a]))/2 - delta_ab tr(Y - Y^+)/6
-    if (F) {
-      for (int task = tid; task < nsites * 9; task += blockDim.x) {
-        const int sl = task / 9, ab = task - sl * 9, a = ab / 3, b = ab - a * 3;
-        const A* Y = ysm + (size_t)sl * 18;
-        const A trim = Y[1] + Y[9] + Y[17];  // Im tr Y; tr(Y - Y^+) = 2 i Im tr Y
-        const A tr_ = (A)0.5 * (Y[(a * 3 + b) * 2] - Y[(b * 3 + a) * 2]);
-        A ti_ = (A)0.5 * (Y[(a * 3 + b) * 2 + 1] + Y[(b * 3 + a) * 2 + 1]);
-        if (a == b) ti_ -= trim / (A)3;
-        double* Fo = F + (lex_sm[sl] * 4 + mu) * 18;
-        Fo[ab * 2] = -(double)tr_;
-        Fo[ab * 2 + 1] = -(double)ti_;
-      }
-    }
+    force_site_algebra<P64, C12, double>(mu, p, first, nsites, Ue, Uo, bsum, usm, ysm, lex_sm, ph_sm, coef, F, G);
     __syncthreads();  // shared memory is reused by the next direction
   }
 }
 
 cudaError_t launch_force(int prec, bool c12, const Geom& g, const void* psi, const void* chi, const void* Ue,
-                         const void* Uo, double* F, double* G, double coef, cudaStream_t st) {
+                         const void* Uo, double* F, double* G, double coef, bool float_float, cudaStream_t st) {
   const int nsg = force_threads_per_site(prec, g.Ls);
   const size_t per_site = force_smem_per_site(prec, nsg);
   int spc = 128 / nsg;
@@ -245,6 +356,13 @@ cudaError_t launch_force(int prec, bool c12, const Geom& g, const void* psi, con
     k_force<P_, true><<<grid, threads, smem, st>>>(g, ps, ch, e, o, F, G, coef, nsg, spc);    \
   else                                                                                         \
     k_force<P_, false><<<grid, threads, smem, st>>>(g, ps, ch, e, o, F, G, coef, nsg, spc);
+  if (prec == P64 && float_float) {
+    if (c12)
+      k_force_ff<true><<<grid, threads, smem, st>>>(g, ps, ch, e, o, F, G, coef, nsg, spc);
+    else
+      k_force_ff<false><<<grid, threads, smem, st>>>(g, ps, ch, e, o, F, G, coef, nsg, spc);
+    return cudaGetLastError();
+  }
   switch (prec) {
     case P64: FK(P64) break;
     case P32: FK(P32) break;

@@ -94,6 +94,15 @@ def test_dhop_float_float_magnitudes(dwf, oracle_lib, scale):
     assert rel(host(op.unpack(op.dhop(f, dwf.FULL))), oracle_lib.dhop(dims, Ls, BC, U, psi)) < TOL
 
 
+def test_float_float_largest_ls(dwf, oracle_lib):
+    dims, Ls = (2, 2, 2, 4), 128
+    op, U = make(dwf, dims, Ls, 15)
+    psi = synth.random_spinor(dims, Ls, seed=16)
+    f = op.pack(dev(psi), 0, dwf.FULL)
+    assert rel(host(op.unpack(op.dhop(f, dwf.FULL))), oracle_lib.dhop(dims, Ls, BC, U, psi)) < TOL
+    assert rel(host(op.unpack(op.m(f))), oracle_lib.m(dims, Ls, M5, MASS, BC, U, psi)) < TOL
+
+
 def test_dhop_float_float_zero_field(dwf):
     dims, Ls = (4, 4, 2, 2), 5
     op, _ = make(dwf, dims, Ls, 47)
@@ -135,6 +144,28 @@ def test_cg_float_float(dwf, oracle_lib, mode):
     xo, _, _, ok = oracle_lib.schur_cg(dims, Ls, M5, MASS, BC, U, b, tol=1e-12, maxiter=20000)
     assert ok
     assert rel(xs, xo) < 1e-7
+
+
+@pytest.mark.parametrize("dims,Ls", [((4, 4, 4, 4), 4), ((2, 4, 2, 6), 3), ((4, 2, 4, 2), 16), ((2, 2, 2, 4), 128)])
+def test_force_float_float(dwf, oracle_lib, dims, Ls):
+    """S = |M psi|^2, its su(3) force and ambient gradient with FP64 fields in float-float."""
+    op, U = make(dwf, dims, Ls, 101)
+    psi = synth.random_spinor(dims, Ls, seed=102)
+    S, F, G = op.force(op.pack(dev(psi), 0, dwf.FULL))
+    S_ref, F_ref, G_ref = oracle_lib.force(dims, Ls, M5, MASS, BC, U, psi)
+    assert abs(S - S_ref) < TOL * S_ref
+    assert rel(host(F), F_ref) < TOL
+    assert rel(host(G), G_ref) < TOL
+
+
+def test_force_float_float_compressed_links(dwf, oracle_lib):
+    dims, Ls = (4, 4, 2, 4), 6
+    op, U = make(dwf, dims, Ls, 105, compress12=True)
+    psi = synth.random_spinor(dims, Ls, seed=106)
+    S, F, G = op.force(op.pack(dev(psi), 0, dwf.FULL))
+    S_ref, F_ref, G_ref = oracle_lib.force(dims, Ls, M5, MASS, BC, U, psi)
+    assert abs(S - S_ref) < TOL * S_ref
+    assert rel(host(F), F_ref) < TOL and rel(host(G), G_ref) < TOL
 
 
 def test_pf_force_float_float(dwf, oracle_lib):

@@ -120,6 +120,23 @@ def test_dhop_parity(dwf, oracle_lib, dims, Ls, eps, prec):
         assert rel(oe[mask], ref[mask]) < TOL[prec]
 
 
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+def test_dhop_largest_ls(dwf, oracle_lib, prec):
+    """Ls = 128, the largest the handle accepts (FP64: one thread per slice fills a CTA)."""
+    dims, Ls = (2, 2, 2, 4), 128
+    op, U = make(dwf, dims, Ls, 13)
+    psi = synth.random_spinor(dims, Ls, seed=14)
+    f = op.pack(dev(psi), prec, dwf.FULL)
+    for dag in (False, True):
+        ref = oracle_lib.dhop(dims, Ls, BC, round_spinor(U, prec), round_spinor(psi, prec), dag=dag)
+        assert rel(host(op.unpack(op.dhop(f, dwf.FULL, dag=dag))), ref) < TOL[prec]
+    _, po = parity_fields(oracle_lib, dims, round_spinor(psi, prec))
+    mask = oracle_lib.parity_mask(dims)
+    out = host(op.unpack(op.mdagm(op.pack(dev(po), prec, dwf.ODD)), subset=dwf.ODD))
+    ref = oracle_lib.mdagm(dims, Ls, M5, MASS, BC, round_spinor(U, prec), po)
+    assert rel(out[mask], ref[mask]) < 8 * TOL[prec]
+
+
 @pytest.mark.parametrize("prec", [2, 3])
 @pytest.mark.parametrize("dims,Ls", [(d, ls) for d, ls, _ in DHOP_CASES] + [((4, 4, 2, 2), 16)])
 def test_dhop_low_precision_storage(dwf, oracle_lib, prec, dims, Ls):
