@@ -469,7 +469,11 @@ def run_cg32(dwf, torch):
     b = op.pack(synth.random_spinor_device(dims, Ls, 1000 * spec["case"] + 2, dev), dwf.FP64, dwf.FULL)
     out = {"workload": "dwf_32x32x32x32_ls16_exp0.5", "tol": 1e-10}
     x64 = None
-    for name, mode in (("mixed_fp32", dwf.CG_MIXED_FP32), ("mixed_fp16", dwf.CG_MIXED_FP16), ("fp64", dwf.CG_FP64)):
+    # *_ff: FP64 operator applications in float-float arithmetic
+    for name, mode, arith in (("mixed_fp32", dwf.CG_MIXED_FP32, 0), ("mixed_fp16", dwf.CG_MIXED_FP16, 0),
+                              ("fp64", dwf.CG_FP64, 0), ("mixed_fp16_ff", dwf.CG_MIXED_FP16, 1),
+                              ("fp64_ff", dwf.CG_FP64, 1)):
+        op.set_fp64_arith(arith)
         x, st = op.cg(b, tol=1e-10, maxiter=20000, mode=mode, raise_on_fail=False)
         out[name] = {"seconds": round(st.seconds, 3), "iterations": st.iterations,
                      "reliable_updates": st.reliable_updates, "true_residual": st.true_residual,

@@ -9,7 +9,7 @@
 #include <string>
 
 #include "../../include/grid_dwf.h"
-#include "dhop_kernel.cuh"
+#include "dhop_ff.cuh"
 #include "site_ops.cuh"
 
 namespace gdwf {

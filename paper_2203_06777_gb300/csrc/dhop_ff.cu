@@ -15,7 +15,7 @@
 //
 // Same operator, layout, thread mapping (one thread per (site, slice)), link staging and fused
 // epilogues (out = post(alpha Dhop in + beta pre(aux))) as the FP64 kernel; see there.
-#include "dhop_kernel.cuh"
+#include "dhop_ff.cuh"
 #include "ff_arith.cuh"
 
 namespace gdwf {

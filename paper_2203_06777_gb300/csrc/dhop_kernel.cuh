@@ -992,12 +992,6 @@ __global__ void __launch_bounds__(DhopOccupancy<P>::THREADS, DhopOccupancy<P>::M
     dhop_body_pair<P, DAG, C12, LSC, EK>(a);
 }
 
-// The FP64 hopping term in float-float arithmetic (dhop_ff.cu): same arguments and launch shape
-// as the FP64 kernel (one thread per (site, slice)), its own shared-memory size.
-size_t dhop_ff_smem_bytes(int sites_per_cta, int Ls, bool post);
-cudaError_t launch_dhop_ff(const DhopArgs& a, bool dag, bool c12, int threads, int blocks, size_t smem,
-                           cudaStream_t stream);
-
 // Host-side launcher, instantiated once per storage precision in its own translation unit.
 template <int P>
 cudaError_t launch_dhop(const DhopArgs& a, bool dag, bool c12, int threads, int blocks, size_t smem,
