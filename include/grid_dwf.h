@@ -94,7 +94,9 @@ int grid_dwf_destroy(grid_dwf_t* h);
 int grid_dwf_set_stream(grid_dwf_t* h, void* stream);
 
 /* Arithmetic of the GRID_DWF_FP64 hopping term (Dhop and everything built on it: M, Mpc,
- * Mpc^+ Mpc, the FP64 CG and the FP64 true residuals of the mixed CG; storage stays FP64).
+ * Mpc^+ Mpc, the FP64 CG and the FP64 true residuals of the mixed CG) and of the FP64 fermion
+ * force (grid_dwf_force, grid_dwf_pf_force with precision GRID_DWF_FP64); storage stays FP64, and
+ * so do the vector updates and reductions of the solvers.
  * GRID_DWF_FP64_ARITH_NATIVE (the default): IEEE double. GRID_DWF_FP64_ARITH_FLOAT_FLOAT: each
  * real carried as an unevaluated sum of two floats (Dekker's double-length arithmetic: error-free
  * TwoSum and FMA-based TwoProduct), about 46 significant bits (relative error of an operator
