@@ -564,7 +564,7 @@ def gpu_arm(args):
             rec["alu_peak_gflops"] = FP64_ALU_TFLOPS * 1e3
         if name == "f64ff":
             rec["arithmetic"] = "float-float (FP64 storage, pairs of FP32 numbers, ~46 significant bits)"
-            rec["bound"] = "alu (FP32 pipe)"
+            rec["bound"] = "instruction issue (FP32, integer and FP64 pipes)"
             if "f64" in variants:
                 rec["speedup_vs_f64"] = round(variants["f64"]["us_per_step"] / rec["us_per_step"], 2)
         results[name] = (secs, steps, launches, per_step, gbs, gflops)
