@@ -8,6 +8,8 @@
 #include <map>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/grid_dwf.h"
 #include "dhop_ff.cuh"
 #include "site_ops.cuh"
@@ -39,6 +41,15 @@ struct grid_dwf {
 };
 
 namespace {
+
+// An NVTX range around each compute entry point, named after it, so that a timeline tool
+// (nsys) shows the ABI calls over their kernels; a no-op when no tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 enum WsId : int {
   WS_TMP_E = 0,
@@ -358,6 +369,7 @@ int grid_dwf_field_bytes(const grid_dwf_t* h, int precision, int subset, size_t*
 }
 
 int grid_dwf_set_gauge(grid_dwf_t* h, const double* U) {
+  const NvtxRange nvtx_("grid_dwf_set_gauge");
   if (!h) return GRID_DWF_ERR_INVALID_ARG;
   if (!U) return fail(h, GRID_DWF_ERR_INVALID_ARG, "U is null");
   const size_t bytes = (size_t)h->g.N4h * 2 * 4 * 18 * sizeof(double);
@@ -375,6 +387,7 @@ int grid_dwf_set_gauge(grid_dwf_t* h, const double* U) {
 }
 
 int grid_dwf_pack(grid_dwf_t* h, int precision, int subset, const double* canonical, void* field) {
+  const NvtxRange nvtx_("grid_dwf_pack");
   if (!h) return GRID_DWF_ERR_INVALID_ARG;
   if (!valid_prec(precision) || subset < 0 || subset > 2) return fail(h, GRID_DWF_ERR_INVALID_ARG, "bad precision/subset");
   RET(check_ptr(h, canonical, "canonical"));
@@ -384,6 +397,7 @@ int grid_dwf_pack(grid_dwf_t* h, int precision, int subset, const double* canoni
 }
 
 int grid_dwf_unpack(grid_dwf_t* h, int precision, int subset, const void* field, double* canonical) {
+  const NvtxRange nvtx_("grid_dwf_unpack");
   if (!h) return GRID_DWF_ERR_INVALID_ARG;
   if (!valid_prec(precision) || subset < 0 || subset > 2) return fail(h, GRID_DWF_ERR_INVALID_ARG, "bad precision/subset");
   RET(check_ptr(h, canonical, "canonical"));
@@ -394,6 +408,7 @@ int grid_dwf_unpack(grid_dwf_t* h, int precision, int subset, const void* field,
 
 int grid_dwf_convert(grid_dwf_t* h, int src_precision, int dst_precision, int subset, const void* src, void* dst,
                      double scale) {
+  const NvtxRange nvtx_("grid_dwf_convert");
   if (!h) return GRID_DWF_ERR_INVALID_ARG;
   if (!valid_prec(src_precision) || !valid_prec(dst_precision) || subset < 0 || subset > 2)
     return fail(h, GRID_DWF_ERR_INVALID_ARG, "bad precision/subset");
@@ -408,6 +423,7 @@ int grid_dwf_convert(grid_dwf_t* h, int src_precision, int dst_precision, int su
 }
 
 int grid_dwf_dhop(grid_dwf_t* h, int precision, const void* in, void* out, int parity, int dag) {
+  const NvtxRange nvtx_("grid_dwf_dhop");
   if (!h) return GRID_DWF_ERR_INVALID_ARG;
   if (!valid_prec(precision) || parity < 0 || parity > 2) return fail(h, GRID_DWF_ERR_INVALID_ARG, "bad precision/parity");
   RET(check_ptr(h, in, "in"));
@@ -425,6 +441,7 @@ int grid_dwf_dhop(grid_dwf_t* h, int precision, const void* in, void* out, int p
 }
 
 int grid_dwf_mooee(grid_dwf_t* h, int precision, int subset, const void* in, void* out, int dag, int inverse) {
+  const NvtxRange nvtx_("grid_dwf_mooee");
   if (!h) return GRID_DWF_ERR_INVALID_ARG;
   if (!valid_prec(precision) || subset < 0 || subset > 2) return fail(h, GRID_DWF_ERR_INVALID_ARG, "bad precision/subset");
   RET(check_ptr(h, in, "in"));
@@ -439,6 +456,7 @@ int grid_dwf_mooee(grid_dwf_t* h, int precision, int subset, const void* in, voi
 }
 
 int grid_dwf_m(grid_dwf_t* h, int precision, const void* in, void* out, int dag) {
+  const NvtxRange nvtx_("grid_dwf_m");
   if (!h) return GRID_DWF_ERR_INVALID_ARG;
   if (!valid_prec(precision)) return fail(h, GRID_DWF_ERR_INVALID_ARG, "bad precision");
   RET(check_ptr(h, in, "in"));
@@ -452,6 +470,7 @@ int grid_dwf_m(grid_dwf_t* h, int precision, const void* in, void* out, int dag)
 }
 
 int grid_dwf_mpc(grid_dwf_t* h, int precision, const void* in, void* out, int dag, void* tmp_even) {
+  const NvtxRange nvtx_("grid_dwf_mpc");
   if (!h) return GRID_DWF_ERR_INVALID_ARG;
   if (!valid_prec(precision)) return fail(h, GRID_DWF_ERR_INVALID_ARG, "bad precision");
   RET(check_ptr(h, in, "in"));
@@ -467,6 +486,7 @@ int grid_dwf_mpc(grid_dwf_t* h, int precision, const void* in, void* out, int da
 }
 
 int grid_dwf_mdagm(grid_dwf_t* h, int precision, const void* in, void* out, void* tmp_odd, void* tmp_even) {
+  const NvtxRange nvtx_("grid_dwf_mdagm");
   if (!h) return GRID_DWF_ERR_INVALID_ARG;
   if (!valid_prec(precision)) return fail(h, GRID_DWF_ERR_INVALID_ARG, "bad precision");
   RET(check_ptr(h, in, "in"));
@@ -487,6 +507,7 @@ int grid_dwf_mdagm(grid_dwf_t* h, int precision, const void* in, void* out, void
 }
 
 int grid_dwf_norm2(grid_dwf_t* h, int precision, int subset, const void* a, double* result) {
+  const NvtxRange nvtx_("grid_dwf_norm2");
   if (!h) return GRID_DWF_ERR_INVALID_ARG;
   if (!valid_prec(precision) || subset < 0 || subset > 2 || !result)
     return fail(h, GRID_DWF_ERR_INVALID_ARG, "bad precision/subset/result");
@@ -499,6 +520,7 @@ int grid_dwf_norm2(grid_dwf_t* h, int precision, int subset, const void* a, doub
 }
 
 int grid_dwf_inner(grid_dwf_t* h, int precision, int subset, const void* a, const void* b, double result[2]) {
+  const NvtxRange nvtx_("grid_dwf_inner");
   if (!h) return GRID_DWF_ERR_INVALID_ARG;
   if (!valid_prec(precision) || subset < 0 || subset > 2 || !result)
     return fail(h, GRID_DWF_ERR_INVALID_ARG, "bad precision/subset/result");
@@ -681,6 +703,7 @@ int cg_normal(grid_dwf_t* h, const void* rhs, void* xo_, double tol, int maxiter
 extern "C" {
 
 int grid_dwf_cg(grid_dwf_t* h, const void* b, void* x, double tol, int maxiter, int mode, grid_dwf_cg_stats* stats) {
+  const NvtxRange nvtx_("grid_dwf_cg");
   if (!h) return GRID_DWF_ERR_INVALID_ARG;
   if (mode < GRID_DWF_CG_FP64 || mode > GRID_DWF_CG_MIXED_BF16 || !(tol > 0) || maxiter < 0)
     return fail(h, GRID_DWF_ERR_INVALID_ARG, "cg: bad mode/tol/maxiter");
@@ -725,6 +748,7 @@ int grid_dwf_cg(grid_dwf_t* h, const void* b, void* x, double tol, int maxiter, 
 }
 
 int grid_dwf_force(grid_dwf_t* h, int precision, const void* psi, void* chi, double* F, double* G, double* S_out) {
+  const NvtxRange nvtx_("grid_dwf_force");
   if (!h) return GRID_DWF_ERR_INVALID_ARG;
   if (precision != GRID_DWF_FP64 && precision != GRID_DWF_FP32)
     return fail(h, GRID_DWF_ERR_INVALID_ARG, "force: precision must be FP64 or FP32");
@@ -752,6 +776,7 @@ int grid_dwf_force(grid_dwf_t* h, int precision, const void* psi, void* chi, dou
 
 int grid_dwf_pf_force(grid_dwf_t* h, const void* phi, void* X, double tol, int maxiter, int mode, int precision,
                       double* F, double* G, double* S_out, grid_dwf_cg_stats* stats) {
+  const NvtxRange nvtx_("grid_dwf_pf_force");
   if (!h) return GRID_DWF_ERR_INVALID_ARG;
   if (mode < GRID_DWF_CG_FP64 || mode > GRID_DWF_CG_MIXED_BF16 || !(tol > 0) || maxiter < 0)
     return fail(h, GRID_DWF_ERR_INVALID_ARG, "pf_force: bad mode/tol/maxiter");
