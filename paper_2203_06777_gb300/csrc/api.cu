@@ -636,17 +636,22 @@ int cg_normal(grid_dwf_t* h, const void* rhs, void* xo_, double tol, int maxiter
     while (!converged && iters < maxiter) {
       RET(mdagm_impl(h, PS, ps, aps, tos, tes));
       CK(launch_reduce(PS, ps, aps, N, Ls, h->partials, h->scal, FIN_ALPHA, 0, h->stream), "cg pAp");
-      CK(launch_cg_xr(GRID_DWF_FP32, PS, xs, rs, ps, aps, N, Ls, h->partials, h->scal, h->stream), "cg update");
+      // r -= alpha Ap now; x += alpha p is deferred to the pass that updates p (one read of p)
+      CK(launch_cg_r(GRID_DWF_FP32, PS, rs, aps, N, Ls, h->partials, h->scal, h->stream), "cg update");
       flops += 4 * half_flops;
       ++iters;
       rr_is_true = false;  // x_s has moved since the last true residual
+      bool reliable = false;
       RET(read_scalars(h));
       const double rr_old_s = rr_s;  // |r_s|^2 before this step (the denominator of beta)
       rr_s = h->host_scal[S_RRNEW];
       if (!is_finite(rr_s)) return fail(h, GRID_DWF_ERR_NONFINITE, "cg: non-finite sloppy residual");
       const double est = std::sqrt(rr_s) / sigma;  // estimated true-scale |r|
       if (rr_s < delta * delta * rr_max || est <= target || iters == maxiter) {
-        // reliable update: fold x_s into x, recompute the true residual in FP64, rescale
+        // reliable update: complete x_s (the pending alpha p), fold it into x, recompute the true
+        // residual in FP64, rescale
+        CK(launch_cg_xp(GRID_DWF_FP32, PS, xs, rs, ps, N, Ls, h->scal, false, h->stream), "cg reliable");
+        reliable = true;
         RET(write_scalar(h, S_TMP0, 1.0 / sigma));
         CK(launch_accum_zero(GRID_DWF_FP32, xo, xs, N, Ls, h->scal + S_TMP0, h->stream), "cg reliable");
         RET(mdagm_impl(h, P, xo, Ap, to, te));
@@ -676,7 +681,10 @@ int cg_normal(grid_dwf_t* h, const void* rhs, void* xo_, double tol, int maxiter
         sigma = sigma_new;
         rr = rr64;
       }
-      CK(launch_cg_p(GRID_DWF_FP32, PS, rs, ps, N, Ls, h->scal, h->stream), "cg p");
+      if (reliable)  // x is complete: p alone (with the rescaled beta)
+        CK(launch_cg_p(GRID_DWF_FP32, PS, rs, ps, N, Ls, h->scal, h->stream), "cg p");
+      else
+        CK(launch_cg_xp(GRID_DWF_FP32, PS, xs, rs, ps, N, Ls, h->scal, true, h->stream), "cg xp");
     }
   }
   // final true residual of the normal equations, FP64 (already known when the loop ended on a

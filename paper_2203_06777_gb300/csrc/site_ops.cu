@@ -505,6 +505,68 @@ __global__ void k_cg_p(const void* r, void* p, long nsites, int Ls, const double
   }
 }
 
+// The mixed solver's inner loop, with the x update deferred by one pass so that p is read once
+// per iteration: k_cg_r forms r -= alpha Ap and |r|^2 (reads r, Ap), then k_cg_xp forms
+// x += alpha p and p = r + beta p from the same read of p (reads x, r, p). Ten field passes per
+// iteration (with p^+ Ap) instead of eleven. k_cg_x applies the pending x update alone, before a
+// reliable update folds x into the FP64 solution.
+template <int PX, int PP>
+__global__ void __launch_bounds__(RED_THREADS) k_cg_r(void* r, const void* Ap, long nsites, int Ls, const double* scal,
+                                                      double* partials) {
+  using RX = RT<PX>;
+  using RP = RT<PP>;
+  const RX alpha = (RX)scal[S_ALPHA];
+  double acc = 0.0;
+  const int Lsh = ls_half(Ls);
+  const long units = nsites * 3 * Lsh;
+  for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < units; u += (long)gridDim.x * blockDim.x) {
+    long site;
+    int g, q;
+    unit_coords(u, Lsh, site, g, q);
+    RX rv[16];
+    RP av[16];
+    ld_unit<PX, true>(r, site, g, q, Lsh, rv);
+    ld_unit<PP, false>(Ap, site, g, q, Lsh, av);
+    RX t = 0;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      rv[j] -= alpha * (RX)av[j];
+      t += rv[j] * rv[j];
+    }
+    st_unit<PX>(r, site, g, q, Lsh, rv);
+    acc += (double)t;
+  }
+  double v[1] = {acc};
+  block_sum<1>(v, partials, RED_BLOCKS);
+}
+
+template <int PX, int PP, bool UPDATE_P>
+__global__ void k_cg_xp(void* x, const void* r, void* p, long nsites, int Ls, const double* scal) {
+  using RX = RT<PX>;
+  using RP = RT<PP>;
+  const RX alpha = (RX)scal[S_ALPHA];
+  const RX beta = (RX)scal[S_BETA];
+  const int Lsh = ls_half(Ls);
+  const long units = nsites * 3 * Lsh;
+  for (long u = blockIdx.x * (long)blockDim.x + threadIdx.x; u < units; u += (long)gridDim.x * blockDim.x) {
+    long site;
+    int g, q;
+    unit_coords(u, Lsh, site, g, q);
+    RX xv[16], rv[16];
+    RP pv[16];
+    ld_unit<PX, true>(x, site, g, q, Lsh, xv);
+    ld_unit<PP, UPDATE_P>(p, site, g, q, Lsh, pv);  // coherent when p is rewritten
+    if (UPDATE_P) ld_unit<PX, false>(r, site, g, q, Lsh, rv);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      xv[j] += alpha * (RX)pv[j];
+      if (UPDATE_P) pv[j] = (RP)(rv[j] + beta * (RX)pv[j]);
+    }
+    st_unit<PX>(x, site, g, q, Lsh, xv);
+    if (UPDATE_P) st_unit<PP>(p, site, g, q, Lsh, pv);
+  }
+}
+
 #define CG_PAIRS(M) \
   M(P64, P64)       \
   M(P32, P32)       \
@@ -522,6 +584,36 @@ cudaError_t launch_cg_xr(int px, int pp, void* x, void* r, const void* p, const 
   }
   CG_PAIRS(XR)
 #undef XR
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_cg_r(int px, int pp, void* r, const void* Ap, long nsites, int Ls, double* partials, double* scal,
+                        cudaStream_t st) {
+#define RU(A, B)                                                                             \
+  if (px == A && pp == B) {                                                                  \
+    k_cg_r<A, B><<<RED_BLOCKS, RED_THREADS, 0, st>>>(r, Ap, nsites, Ls, scal, partials);    \
+    cudaError_t e = cudaGetLastError();                                                      \
+    if (e != cudaSuccess) return e;                                                          \
+    return finalize(partials, 1, scal, FIN_BETA, 0, st);                                     \
+  }
+  CG_PAIRS(RU)
+#undef RU
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_cg_xp(int px, int pp, void* x, const void* r, void* p, long nsites, int Ls, const double* scal,
+                         bool update_p, cudaStream_t st) {
+  const int blocks = grid_for(nsites * 3 * ls_half(Ls), 256);
+#define XP(A, B)                                                                                        \
+  if (px == A && pp == B) {                                                                             \
+    if (update_p)                                                                                       \
+      k_cg_xp<A, B, true><<<blocks, 256, 0, st>>>(x, r, p, nsites, Ls, scal);                          \
+    else                                                                                                \
+      k_cg_xp<A, B, false><<<blocks, 256, 0, st>>>(x, r, p, nsites, Ls, scal);                         \
+    return cudaGetLastError();                                                                          \
+  }
+  CG_PAIRS(XP)
+#undef XP
   return cudaErrorInvalidValue;
 }
 

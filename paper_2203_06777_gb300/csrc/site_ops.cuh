@@ -49,6 +49,11 @@ cudaError_t launch_reduce(int prec, const void* a, const void* b, long nsites, i
 cudaError_t launch_cg_xr(int px, int pp, void* x, void* r, const void* p, const void* Ap, long nsites, int Ls,
                          double* partials, double* scal, cudaStream_t st);
 // p = r + beta p.
+// r -= alpha Ap and |r|^2 (finalised as FIN_BETA); x += alpha p, then (update_p) p = r + beta p.
+cudaError_t launch_cg_r(int px, int pp, void* r, const void* Ap, long nsites, int Ls, double* partials, double* scal,
+                        cudaStream_t st);
+cudaError_t launch_cg_xp(int px, int pp, void* x, const void* r, void* p, long nsites, int Ls, const double* scal,
+                         bool update_p, cudaStream_t st);
 cudaError_t launch_cg_p(int px, int pp, const void* r, void* p, long nsites, int Ls, const double* scal,
                         cudaStream_t st);
 // r = b - Ax (FP64) and |r|^2 -> scal[dst].
