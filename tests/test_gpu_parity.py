@@ -518,3 +518,32 @@ def test_force_8x8x8x8_ls8_fd_and_oracle(dwf, oracle_lib):
             fd = (vals[0] - vals[1]) / (2 * hstep)
             an = (np.conj(Gh[idx]) * unit).real
             assert abs(fd - an) < 1e-9 * abs(an) + 1e-12 * S / hstep, (fd, an)
+
+
+# ---------------------------------------------------------------- random-shape sweep
+# Seeded random lattice shapes (each extent 2, 4 or 6; Ls in 1..16) against the oracle: ragged
+# half lattices, odd Ls (pad slice), tail launches and every Ls specialisation and the generic
+# kernel, for the hopping term (both signs) and the full M.
+
+def _random_shapes(n=12, seed=2203):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        dims = tuple(int(v) for v in rng.choice([2, 4, 6], size=4))
+        Ls = int(rng.choice([1, 2, 3, 4, 5, 8, 12, 16]))
+        out.append((dims, Ls))
+    return out
+
+
+@pytest.mark.parametrize("dims,Ls", _random_shapes())
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+def test_random_shape_sweep(dwf, oracle_lib, dims, Ls, prec):
+    op, U = make(dwf, dims, Ls, 301, eps=0.4)
+    psi = synth.random_spinor(dims, Ls, seed=302)
+    f = op.pack(dev(psi), prec, dwf.FULL)
+    psi_r, U_r = round_spinor(psi, prec), round_spinor(U, prec)
+    for dag in (False, True):
+        ref = oracle_lib.dhop(dims, Ls, BC, U_r, psi_r, dag=dag)
+        assert rel(host(op.unpack(op.dhop(f, dwf.FULL, dag=dag))), ref) < TOL[prec], ("dhop", dag)
+    ref = oracle_lib.m(dims, Ls, M5, MASS, BC, U_r, psi_r)
+    assert rel(host(op.unpack(op.m(f))), ref) < 2 * TOL[prec], "m"
