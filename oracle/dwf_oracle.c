@@ -556,8 +556,8 @@ double dwf_oracle_force(const int dims[4], int Ls, double M5, double mass, const
 
 /*
  * Two-flavour pseudofermion action on odd sites, S = phi^+ (Mpc^+ Mpc)^-1 phi, and its
- * derivative with respect to the links (the survey's next-step row: the operator used inside
- * hybrid Monte Carlo, differentiated through the solve).
+ * derivative with respect to the links: the action that hybrid Monte Carlo integrates,
+ * differentiated through the solve.
  *
  * X = (Mpc^+ Mpc)^-1 phi by plain conjugate gradients from X = 0, stopping when the recursive
  * residual satisfies |r| <= tol |phi|; S = Re phi^+ X; Y = Mpc X. Only the hopping blocks of Mpc
