@@ -45,6 +45,11 @@ def main():
     out["mdagm"] = {"norm2": oracle.norm2(mdm)}
     out["force"] = {"S": S, "F_norm2": oracle.norm2(F), "G_norm2": oracle.norm2(G),
                     "F_000_mu3": [[float(z.real), float(z.imag)] for z in F[0, 0, 0, 0, 3].ravel()]}
+    # pseudofermion action phi^+ (Mpc^+ Mpc)^-1 phi on the odd sites of the same spinor
+    phi = psi * oracle.parity_mask(DIMS)[..., None, None, None]
+    Spf, X, Fpf, Gpf, _ = oracle.pf_force(DIMS, LS, M5, MASS, BC, U, phi, tol=1e-14, maxiter=100000)
+    out["pf_force"] = {"tol": 1e-14, "S": Spf, "X_norm2": oracle.norm2(X), "F_norm2": oracle.norm2(Fpf),
+                       "G_norm2": oracle.norm2(Gpf)}
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_2x2x2x4_ls4.json")
     with open(path, "w") as fh:
         json.dump(out, fh, indent=1)

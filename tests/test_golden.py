@@ -34,3 +34,11 @@ def test_oracle_golden_values(oracle_lib):
     assert np.isclose(oracle_lib.norm2(G), g["force"]["G_norm2"], rtol=1e-12)
     f0 = np.array([[z.real, z.imag] for z in F[0, 0, 0, 0, 3].ravel()])
     assert np.allclose(f0, np.array(g["force"]["F_000_mu3"]), rtol=1e-12, atol=1e-13)
+    # the pseudofermion action and its force (an iterative solve to 1e-14: compared at 1e-10)
+    phi = psi * oracle_lib.parity_mask(dims)[..., None, None, None]
+    pf = g["pf_force"]
+    Spf, X, Fpf, Gpf, _ = oracle_lib.pf_force(dims, Ls, M5, mass, bc, U, phi, tol=pf["tol"], maxiter=100000)
+    assert np.isclose(Spf, pf["S"], rtol=1e-10)
+    assert np.isclose(oracle_lib.norm2(X), pf["X_norm2"], rtol=1e-10)
+    assert np.isclose(oracle_lib.norm2(Fpf), pf["F_norm2"], rtol=1e-10)
+    assert np.isclose(oracle_lib.norm2(Gpf), pf["G_norm2"], rtol=1e-10)
