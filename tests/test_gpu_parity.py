@@ -268,6 +268,28 @@ def test_cg_solves_full_system(dwf, oracle_lib, mode):
     assert rel(xs, xo) < 1e-7
 
 
+@pytest.mark.parametrize("mode", [1, 2])
+def test_mixed_cg_stopped_by_maxiter(dwf, oracle_lib, mode):
+    """A mixed solve cut short by maxiter: not converged, and the returned x is the folded
+    solution whose true residual the stats report (recomputed here by the oracle)."""
+    dims, Ls = (4, 4, 4, 4), 8
+    op, U = make(dwf, dims, Ls, 95, eps=0.4)
+    b = synth.random_spinor(dims, Ls, seed=96)
+    fb = op.pack(dev(b), 0, dwf.FULL)
+    x, st = op.cg(fb, tol=1e-12, maxiter=7, mode=mode, raise_on_fail=False)
+    assert not st.converged and st.iterations == 7
+    xs = host(op.unpack(x))
+    assert np.all(np.isfinite(xs))
+    # the Schur normal-equation residual of x_o reported by the solver, against the oracle's
+    mask = oracle_lib.parity_mask(dims)[..., None, None, None]
+    be, bo = b * ~mask, b * mask
+    bp = bo + 0.5 * oracle_lib.dhop(dims, Ls, BC, U, oracle_lib.mooee(dims, Ls, M5, MASS, be, inverse=True)) * mask
+    rhs = oracle_lib.mpc(dims, Ls, M5, MASS, BC, U, bp, dag=True)
+    r = rhs - oracle_lib.mdagm(dims, Ls, M5, MASS, BC, U, xs * mask)
+    true_res = np.linalg.norm(r[mask[..., 0, 0, 0]]) / np.linalg.norm(rhs[mask[..., 0, 0, 0]])
+    assert abs(true_res - st.true_residual) < 1e-6 * true_res + 1e-14
+
+
 # ---------------------------------------------------------------- force
 
 
