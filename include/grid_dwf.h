@@ -190,8 +190,10 @@ int grid_dwf_pf_force(grid_dwf_t* h, const void* phi, void* X, double tol, int m
  * library's device image, present on every GPU that loads the library until the process exits.
  * The paper has no counterpart; this is a service of the library.
  *   a, b      device fields of `precision` in the device layout (16-byte aligned), nsites
- *             checkerboard site blocks of Ls slices each, padded to even as in every field of
- *             this library (V/2 site blocks for a half field, V for a full one);
+ *             checkerboard sites of Ls slices each, padded to even as in every field of this
+ *             library (V/2 sites for a half field, V for a full one). nsites must be a multiple
+ *             of 4, since the layout stores sites in blocks of 4 (every half field of an even
+ *             lattice is); any other nsites is GRID_DWF_ERR_INVALID_ARG before any launch;
  *   result    device pointer to 2 doubles (8-byte aligned), receives (re, im) (im = 0 for |a|^2);
  *   stream    cudaStream_t the two kernels run on (NULL = legacy default stream); asynchronous;
  *   err       optional buffer for a message on failure.
@@ -199,7 +201,10 @@ int grid_dwf_pf_force(grid_dwf_t* h, const void* phi, void* X, double tol, int m
  * 32^4 x 16 full field, 16777216); larger fields are rejected with GRID_DWF_ERR_INVALID_ARG
  * before anything runs. The first call
  * on a device looks up the array's device address (once per device, with that device current);
- * make that first call before any stream capture. All calls share the one array, which keeps the
+ * make that first call before any stream capture. The address is cached per device index for the
+ * life of the process: the library assumes the device's primary context (the one the CUDA
+ * runtime uses) and no cudaDeviceReset between calls, since a reset or a different context
+ * would leave the cached address stale. All calls share the one array, which keeps the
  * last call's partial sums (each call overwrites what it reads), so calls whose kernels overlap
  * on the GPU (on different streams, or different host threads) race and give wrong results. */
 int grid_dwf_inner_noalloc(int precision, const void* a, const void* b, long nsites, int Ls, void* stream,

@@ -837,6 +837,12 @@ extern "C" int grid_dwf_inner_noalloc(int precision, const void* a, const void* 
     return noalloc_error(err, err_len, GRID_DWF_ERR_INVALID_ARG, "grid_dwf_inner_noalloc: bad precision");
   if (!a || !result || nsites < 0 || Ls < 1)
     return noalloc_error(err, err_len, GRID_DWF_ERR_INVALID_ARG, "grid_dwf_inner_noalloc: null pointer or bad size");
+  // Sites are stored in blocks of SITE_BLOCK: a partial last block would make the kernel read the
+  // chunks of a whole block past the end of a buffer sized for nsites sites.
+  if (nsites % SITE_BLOCK != 0)
+    return noalloc_error(err, err_len, GRID_DWF_ERR_INVALID_ARG,
+                         "grid_dwf_inner_noalloc: nsites must be a multiple of " + std::to_string(SITE_BLOCK) +
+                             " (fields hold whole blocks of 4 checkerboard sites)");
   if (reinterpret_cast<uintptr_t>(a) % 16 || (b && reinterpret_cast<uintptr_t>(b) % 16) ||
       reinterpret_cast<uintptr_t>(result) % 8)
     return noalloc_error(err, err_len, GRID_DWF_ERR_INVALID_ARG, "grid_dwf_inner_noalloc: misaligned pointer");

@@ -67,3 +67,20 @@ def test_build_uses_sm103a_only():
     from paper_2203_06777_gb300 import _build
 
     assert "arch=compute_103a,code=sm_103a" in " ".join(_build.NVCC_FLAGS)
+
+
+def test_noalloc_rejects_partial_site_blocks_on_the_host(lib):
+    """grid_dwf_inner_noalloc refuses an nsites that is not whole blocks of 4 sites before any CUDA
+    call (the pointers below are never dereferenced): a partial block would be read past the end
+    of a buffer sized for nsites sites."""
+    f = lib.grid_dwf_inner_noalloc
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_long, ctypes.c_int, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t]
+    err = ctypes.create_string_buffer(256)
+    fake = ctypes.c_void_p(1 << 20)  # aligned, never read
+    for nsites in (1, 2, 3, 5, 6, 7, 4097):
+        assert f(1, fake, None, nsites, 16, None, fake, err, 256) == -1
+        assert b"multiple of 4" in err.value
+    assert f(1, fake, None, -4, 16, None, fake, err, 256) == -1
+    assert f(7, fake, None, 4, 16, None, fake, err, 256) == -1  # bad precision

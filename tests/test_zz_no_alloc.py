@@ -42,9 +42,14 @@ def noalloc(dwf, prec, a, b, nsites, Ls, out):
     return rc, err.value.decode()
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2, 3])
-def test_noalloc_matches_handle_reductions_twice_in_a_row(dwf, prec):
-    dims, Ls = (8, 4, 4, 6), 8
+# Ls 8 in every precision; odd Ls 7 (a zero pad slice in every site, written by pack) and Ls 12
+# in FP64 and FP32.
+NOALLOC_CASES = [(0, 8), (1, 8), (2, 8), (3, 8), (0, 7), (1, 7), (1, 12)]
+
+
+@pytest.mark.parametrize("prec,Ls", NOALLOC_CASES)
+def test_noalloc_matches_handle_reductions_twice_in_a_row(dwf, prec, Ls):
+    dims = (8, 4, 4, 6)
     op = dwf.GridDWF(dims, Ls, 1.8, 0.01)
     a = op.pack(torch.from_numpy(synth.random_spinor(dims, Ls, seed=201)).cuda(), prec, dwf.FULL)
     b = op.pack(torch.from_numpy(synth.random_spinor(dims, Ls, seed=202)).cuda(), prec, dwf.FULL)
@@ -76,8 +81,11 @@ def test_noalloc_rejects_fields_beyond_the_static_scratch(dwf):
     out = torch.zeros(2, dtype=torch.float64, device="cuda")
     a = torch.zeros(4 * 16 * 24, dtype=torch.float32, device="cuda")  # 4 sites x Ls 16, FP32
     # the size check runs on the host before any launch, so the small buffer is never read
-    rc, msg = noalloc(dwf, 1, a, None, MAX_SITES_X_LS // 16 + 1, 16, out)
+    rc, msg = noalloc(dwf, 1, a, None, (MAX_SITES_X_LS // 16 // 4 + 1) * 4, 16, out)  # whole blocks
     assert rc == -1 and "exceeds the static scratch" in msg
+    # nsites must be whole blocks of 4 sites: 5 would read a block past the end of the buffer
+    rc, msg = noalloc(dwf, 1, a, None, 5, 16, out)
+    assert rc == -1 and "multiple of 4" in msg
     rc, msg = noalloc(dwf, 1, a, None, 4, 16, out)
     assert rc == 0, msg
     torch.cuda.synchronize()
