@@ -11,7 +11,7 @@ L2 hygiene: each step works on one of three independent sets (operator with its 
 input and output fields; 3 x 221 MB in FP32), used round-robin, so every step's inputs were last
 touched two steps earlier and have been evicted from the 126 MiB L2 by the other sets' traffic.
 
-Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--no-cg]
+Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--no-cg] [--no-cg32] [--no-sweep]
 Under torchrun each rank runs the same workload on its own GPU (replicas: the operator has no
 data-path collective); rank 0 prints one JSON line with the aggregate over ranks.
 """
@@ -52,10 +52,16 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# FP64 arithmetic ceiling of this part: a DFMA throughput loop over all 152 SMs (2 flops per
-# DFMA, no FP64 tensor path) measured 1.17 TFLOP/s on a GB300. Dhop issues about 860 FP64 instructions per
-# 1320 flops, so its own ceiling is about 0.9 TFLOP/s.
-FP64_ALU_TFLOPS = 1.17
+def pipe_peaks(dwf):
+    """FMA throughput of this GPU measured by the library's own loop kernels (grid_dwf_pipe_peak):
+    the FP64 ceiling is the roofline of the IEEE FP64 hopping term, which this part's FP64 pipe
+    bounds (no FP64 tensor path is used); FP32 scalar / packed FP32x2 for context."""
+    names = (("fp64_fma_gflops", dwf.PEAK_FP64_FMA), ("fp32_fma_gflops", dwf.PEAK_FP32_FMA),
+             ("fp32x2_fma_gflops", dwf.PEAK_FP32X2_FMA))
+    out = {k: round(dwf.pipe_peak(v), 1) for k, v in names}
+    out["method"] = ("grid_dwf_pipe_peak: 8 independent FMA chains x 4096 trips per thread, 8 CTAs x 256 threads "
+                     "per SM, best of 3 CUDA-event timings after a warm-up; 2 flops per FMA, 4 per packed FMA")
+    return out
 
 
 KERNEL_SOURCES = ["paper_2203_06777_gb300/csrc/dhop_kernel.cuh", "paper_2203_06777_gb300/csrc/dhop_inst.cuh",
@@ -124,6 +130,17 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+
+    def wait_first_sample(self, timeout=3.0):
+        t0 = time.time()
+        while self.proc and not self.lines and time.time() - t0 < timeout:
+            time.sleep(0.01)
+
+    def wait_next_sample(self, timeout=1.0):
+        n = len(self.lines)
+        t0 = time.time()
+        while self.proc and len(self.lines) == n and time.time() - t0 < timeout:
+            time.sleep(0.01)
 
     def __exit__(self, *a):
         if self.proc:
@@ -218,6 +235,18 @@ def launches_per_step(op, prec, dwf) -> int:
     lsh = (op.Ls + 1) // 2
     spc = min(max(1, 128 // lsh), op.half_sites)
     return 1 if op.half_sites % spc == 0 else 2
+
+
+def soak(dwf, torch, sets, seconds):
+    """Run the step untimed for about `seconds` (clock sampling; not part of any timing)."""
+    t0 = time.perf_counter()
+    i = 0
+    while time.perf_counter() - t0 < seconds:
+        for _ in range(20):
+            op, src, dst = sets[i % len(sets)]
+            op.dhop(src, dwf.FULL, out=dst)
+            i += 1
+        torch.cuda.synchronize()
 
 
 def time_dhop(dwf, torch, sets, steps, warmup, world):
@@ -415,7 +444,7 @@ def run_pf_force(dwf, torch, spec):
     return out
 
 
-def run_sweep32(dwf, torch, steps=20, warmup=3):
+def run_sweep32(dwf, torch, steps=20, warmup=3, fp64_peak=None):
     """Roofline sweep of DhopEO + DhopOE at 32^4 x 16 (exp(0.5 i H) links, m = 0.005): FP32, FP16,
     BF16 and FP64 storage. One operand set: a 32^4 x 16 half field (805 MB in FP32) is larger than
     L2, so no rotation is needed. Fields are drawn on the device by the seeded generators."""
@@ -435,7 +464,7 @@ def run_sweep32(dwf, torch, steps=20, warmup=3):
         src = op.pack(psi, prec, dwf.FULL)
         dst = op.field(prec, dwf.FULL, zero=True)
         half = op.half_reals
-        n = steps if name != "f64" else max(2, steps // 10)
+        n = steps
         for _ in range(warmup):
             op.dhop(src, dwf.FULL, out=dst)
         torch.cuda.synchronize()
@@ -449,8 +478,8 @@ def run_sweep32(dwf, torch, steps=20, warmup=3):
         gbs = algorithmic_bytes_per_site(rb, Ls) * n5 / per_half / 1e9
         rec = {"us_per_half_lattice": round(per_half * 1e6, 2), "gflops": round(FLOPS_PER_SITE * n5 / per_half / 1e9, 1),
                "algorithmic_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4)}
-        if name == "f64":
-            rec["alu_frac"] = round(rec["gflops"] / (FP64_ALU_TFLOPS * 1e3), 4)
+        if name == "f64" and fp64_peak:
+            rec["alu_frac"] = round(rec["gflops"] / fp64_peak, 4)
         out[name] = rec
         del src, dst
     op.close()
@@ -460,7 +489,7 @@ def run_sweep32(dwf, torch, steps=20, warmup=3):
 
 def run_cg32(dwf, torch):
     """Mixed-precision vs FP64 CG at 32^4 x 16, m = 0.005, exp(0.5 i H) links, one Gaussian source,
-    to a 1e-10 true residual (optional: the FP64 solve takes tens of seconds)."""
+    to a 1e-10 true residual (on by default; --no-cg32 skips it: the IEEE FP64 solve takes about 14 s)."""
     spec = synth.WORKLOADS["dwf_32x32x32x32_ls16_exp0.5"]
     dims, Ls = spec["dims"], spec["Ls"]
     dev = torch.device("cuda")
@@ -487,6 +516,40 @@ def run_cg32(dwf, torch):
     out["speedup_mixed_fp16_vs_fp64"] = round(out["fp64"]["seconds"] / out["mixed_fp16"]["seconds"], 2)
     op.close()
     return out
+
+
+def profile_case(args):
+    """A fixed, short launch sequence for a profiler (ncu): the full-lattice Dhop of one precision
+    on the named workload, 3 warm-up calls then 3 more, fields drawn on the device. Prints one line
+    with the CUDA-event time of the last three (a number taken under a profiler is not a result)."""
+    import torch
+
+    from paper_2203_06777_gb300 import dwf
+
+    torch.cuda.set_device(0)
+    spec = synth.WORKLOADS[args.profile]
+    dims, Ls = spec["dims"], spec["Ls"]
+    prec = {"f32": dwf.FP32, "f16": dwf.FP16, "bf16": dwf.BF16, "f64": dwf.FP64, "f64ff": dwf.FP64}[args.variants.split(",")[0]]
+    dev = torch.device("cuda")
+    op = dwf.GridDWF(dims, Ls, spec["M5"], spec["mass"], bc=BC,
+                     fp64_arith=dwf.FP64_ARITH_FLOAT_FLOAT if args.variants.startswith("f64ff") else 0)
+    op.set_gauge(synth.random_gauge_device(dims, 1000 * spec["case"], spec["eps"] or 0.3, dev))
+    src = op.pack(synth.random_spinor_device(dims, Ls, 1000 * spec["case"] + 1, dev), prec, dwf.FULL)
+    dst = op.field(prec, dwf.FULL, zero=True)
+    torch.cuda.empty_cache()  # only the fields, links and workspaces stay on the device
+    for _ in range(3):
+        op.dhop(src, dwf.FULL, out=dst)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        op.dhop(src, dwf.FULL, out=dst)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": args.profile, "variant": args.variants.split(",")[0],
+                      "us_per_call": round(e0.elapsed_time(e1) * 1e3 / 3, 2),
+                      "launches_per_call": launches_per_step(op, prec, dwf)}), flush=True)
+    op.close()
 
 
 def cpu_baseline_sample(spec, target_seconds=10.0):
@@ -530,6 +593,7 @@ def gpu_arm(args):
     dims, Ls = spec["dims"], spec["Ls"]
     n5 = int(np.prod(dims)) // 2 * Ls
     hbm_peak, peak_kind = peaks()
+    peaks_alu = pipe_peaks(dwf)
     variants = {}
     results = {}
     clocks = None
@@ -541,11 +605,18 @@ def gpu_arm(args):
             continue
         arith = dwf.FP64_ARITH_FLOAT_FLOAT if name == "f64ff" else dwf.FP64_ARITH_NATIVE
         sets = make_sets(dwf, torch, spec, prec, 3, seed0=0, fp64_arith=arith)
-        steps = args.steps if name not in ("f64", "f64ff") else max(3, args.steps // (40 if name == "f64" else 10))
+        steps = args.steps
         if name == "f32":
             with ClockSampler(torch.cuda.current_device()) as cs:
+                # The sampler reads nvidia-smi every 50 ms; a short timed region (20 steps take about
+                # 1 ms) would see no sample, so the same step runs untimed for ~0.3 s first (clocks at
+                # their loaded value) and the sampler's window brackets that soak and the timed region.
+                cs.wait_first_sample()
+                soak(dwf, torch, sets, 0.3)
                 secs = time_dhop(dwf, torch, sets, steps, args.warmup, world)
+                cs.wait_next_sample()
             clocks = cs.summary()
+            clocks["window"] = "0.3 s untimed soak of the same step, the warm-up and the timed region"
         else:
             secs = time_dhop(dwf, torch, sets, steps, args.warmup, world)
         secs = reduce_max(secs, world)
@@ -559,9 +630,10 @@ def gpu_arm(args):
                "us_per_half_lattice": round(per_step / 2 * 1e6, 2), "launches_per_step": launches // steps,
                "bytes_per_site": bytes_site, "steps": steps}
         if name == "f64":
-            rec["alu_frac"] = round(gflops / (FP64_ALU_TFLOPS * 1e3), 4)
+            rec["alu_frac"] = round(gflops / peaks_alu["fp64_fma_gflops"], 4)
             rec["bound"] = "alu"
-            rec["alu_peak_gflops"] = FP64_ALU_TFLOPS * 1e3
+            rec["alu_peak_gflops"] = peaks_alu["fp64_fma_gflops"]
+            rec["alu_peak_kind"] = "measured (grid_dwf_pipe_peak, FP64 FMA)"
         if name == "f64ff":
             rec["arithmetic"] = "float-float (FP64 storage, pairs of FP32 numbers, ~46 significant bits)"
             rec["bound"] = "instruction issue (FP32, integer and FP64 pipes)"
@@ -570,7 +642,7 @@ def gpu_arm(args):
         results[name] = (secs, steps, launches, per_step, gbs, gflops)
         variants[name] = rec
         if name == "f32":
-            e2e_steps = max(3, args.steps // 20)
+            e2e_steps = args.steps
             e2e_secs, hb, db = time_dhop_e2e(dwf, torch, sets, e2e_steps, args.warmup, world)
             e2e_secs = reduce_max(e2e_secs, world)
             e2e = {"value": round(world * FLOPS_PER_SITE * 2 * n5 * e2e_steps / e2e_secs / 1e9, 1), "unit": "GFlop/s",
@@ -613,9 +685,20 @@ def gpu_arm(args):
     }
     if not args.no_cg and rank == 0:
         line["cg"] = run_cg(dwf, torch, synth.WORKLOADS[CG_WORKLOAD])
+    line["pipe_peaks"] = peaks_alu
     if not args.no_sweep and rank == 0:
-        line["sweep_32x32x32x32_ls16"] = run_sweep32(dwf, torch)
-    if args.cg32 and rank == 0:
+        sw = run_sweep32(dwf, torch, fp64_peak=peaks_alu["fp64_fma_gflops"])
+        line["sweep_32x32x32x32_ls16"] = sw
+        # the largest single-GPU workload's headline: the same kernel on the 32^4 x 16 lattice
+        # (half field 805 MB in FP32, larger than L2: one operand set)
+        f32 = sw["f32"]
+        line["roofline_32x32x32x32_ls16"] = {
+            "bound": "hbm", "achieved": f32["algorithmic_gbs"], "peak": hbm_peak, "unit": "GB/s",
+            "frac": f32["hbm_frac"], "traffic": None, "peak_kind": peak_kind,
+            "kernel": "dhop_kernel<FP32> (DhopEO + DhopOE in one launch)", "gflops": f32["gflops"],
+            "bytes_per_launch": algorithmic_bytes_per_site(4, 16) * 2 * (32 ** 4 // 2) * 16,
+            "us_per_launch": round(2 * f32["us_per_half_lattice"], 2), "steps": sw["steps"]}
+    if not args.no_cg32 and rank == 0:
         line["cg_32x32x32x32_ls16"] = run_cg32(dwf, torch)
     if not args.no_force and rank == 0:
         line["force"] = run_force(dwf, torch, synth.WORKLOADS["dwf_16x16x16x16_ls16_haar"])
@@ -678,12 +761,16 @@ def main(argv=None):
     ap.add_argument("--no-cg", action="store_true", help="skip the CG time-to-solution comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-sweep", action="store_true", help="skip the 32^4 x 16 Dhop roofline sweep")
-    ap.add_argument("--cg32", action="store_true", help="also run the 32^4 x 16 mixed vs FP64 CG (slow)")
+    ap.add_argument("--no-cg32", action="store_true", help="skip the 32^4 x 16 mixed vs FP64 CG (about 25 s)")
     ap.add_argument("--no-force", action="store_true", help="skip the action/force and pseudofermion force timing")
+    ap.add_argument("--profile", default=None, help="run only a short Dhop launch sequence of this workload "
+                    "(a synth.WORKLOADS name) for a profiler, in the first precision of --variants")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
-    if args.impl == "reference":
+    if args.profile:
+        profile_case(args)
+    elif args.impl == "reference":
         reference_arm(args)
     else:
         gpu_arm(args)

@@ -128,35 +128,65 @@ int grid_dwf_convert(grid_dwf_t* h, int src_precision, int dst_precision, int su
 
 /* Hopping term. parity GRID_DWF_EVEN: out (even half) = DhopEO in (odd half); GRID_DWF_ODD:
  * out (odd) = DhopOE in (even); GRID_DWF_FULL: full fields, both halves. dag != 0: Dhop^+.
- * 1320 flops per output 5D site. */
+ * 1320 flops per output 5D site.
+ * Source: the "main kernel DWF code" of the paper's Section 3 (Nsight-Compute figure: about 80%
+ * of peak memory bandwidth, 39% of the floating-point pipe) and the Conclusion's node-local
+ * "Wilson" matrix; the paper prints no formula, so the definition is the Dhop formula above
+ * (chiral gamma basis, (1 - gamma_mu) on the forward hop, bc[mu] on hops crossing the edge). */
 int grid_dwf_dhop(grid_dwf_t* h, int precision, const void* in, void* out, int parity, int dag);
 
 /* Fifth-dimension operator on a field of `subset`: Mooee, Mooee^+ (dag), Mooee^-1 (inverse) or
- * (Mooee^+)^-1. In-place use (in == out) is allowed. */
+ * (Mooee^+)^-1. In-place use (in == out) is allowed.
+ * Source: one of "all kernels involved in the DWF Dirac operator" of the paper's Conclusion and
+ * Section 3 (Nsight-Systems figure); no formula is printed, so this is the Shamir term of the
+ * preamble: (5 - M5) on the diagonal, P- coupling s to s+1 and P+ coupling s to s-1 with +m on
+ * the wrap-around; Mooee^+ is its transpose in s, Mooee^-1 the closed-form inverse of the cyclic
+ * bidiagonal matrix of each chirality. */
 int grid_dwf_mooee(grid_dwf_t* h, int precision, int subset, const void* in, void* out, int dag, int inverse);
 
-/* Full operator on full fields: out = M in, or M^+ in (dag). */
+/* Full operator on full fields: out = M in, or M^+ in (dag).
+ * Source: the DWF Dirac operator of the paper's Introduction and Section 3; the reading is
+ * M = Mooee - Dhop/2 (Shamir, preamble), in one launch (Dhop with Mooee fused in). */
 int grid_dwf_m(grid_dwf_t* h, int precision, const void* in, void* out, int dag);
 
 /* Odd-site Schur complement on odd half fields: out = Mpc in (dag: Mpc^+ in). tmp_even: an even
- * half field of scratch, or NULL for a handle-owned one. */
+ * half field of scratch, or NULL for a handle-owned one.
+ * Source: the red-black preconditioned form in which the paper's Section 3 runs the DWF operator
+ * (the Nsight-Systems "sequence" of kernels); reading: Mpc = Mooee - Moe Mooee^-1 Meo with
+ * Meo = -D_eo/2, Moe = -D_oe/2, Mpc^+ = Mooee^+ - Meo^+ (Mooee^-1)^+ Moe^+ (two launches each). */
 int grid_dwf_mpc(grid_dwf_t* h, int precision, const void* in, void* out, int dag, void* tmp_even);
 
-/* out = Mpc^+ Mpc in on odd half fields. tmp_odd / tmp_even: scratch half fields or NULL. */
+/* out = Mpc^+ Mpc in on odd half fields. tmp_odd / tmp_even: scratch half fields or NULL.
+ * Source: as grid_dwf_mpc; the Hermitian positive-definite normal operator that CG inverts
+ * (four launches: each Dhop with its Mooee / Mooee^-1 step fused). */
 int grid_dwf_mdagm(grid_dwf_t* h, int precision, const void* in, void* out, void* tmp_odd, void* tmp_even);
 
-/* Reductions with FP64 accumulation, bitwise reproducible: |a|^2, and a^+ b as (re, im). */
+/* Reductions with FP64 accumulation, bitwise reproducible: |a|^2, and a^+ b as (re, im).
+ * Source: the reduction primitive of the paper's Section 2.1 (accelerator_sum); here a fixed
+ * two-pass order (608 partial sums, then one CTA) so that repeated calls agree bit for bit. */
 int grid_dwf_norm2(grid_dwf_t* h, int precision, int subset, const void* a, double* result);
 int grid_dwf_inner(grid_dwf_t* h, int precision, int subset, const void* a, const void* b, double result[2]);
 
-/* Solve M x = b (full FP64 fields in device layout) through the odd-site Schur complement:
+/* Source: the paper describes no solver; this is the standard use of the operator it profiles
+ * (conjugate gradient on the Schur normal equations), with these readings: stop on the FP64
+ * true relative residual of the normal equations (1e-10 in the benchmarks); the mixed modes are
+ * FP64 defect correction with reliable updates: the inner CG runs on vectors rescaled to unit
+ * rms element, in FP32 (r, x) and the storage precision (p, A p), and the FP64 residual is
+ * recomputed when the inner one has fallen by 1e-3 (FP32) or 0.03 (FP16 / BF16) since the last
+ * recomputation, or when it predicts convergence.
+ * Solve M x = b (full FP64 fields in device layout) through the odd-site Schur complement:
  *   b'_o = b_o - Moe Mooee^-1 b_e; CG on Mpc^+ Mpc x_o = Mpc^+ b'_o; x_e = Mooee^-1 (b_e - Meo x_o).
  * x holds the initial guess on input (its odd half is used). Stops when the FP64 true residual
  * of the normal equations falls to tol; returns GRID_DWF_ERR_NOT_CONVERGED (x and *stats still
  * filled) after maxiter iterations. stats may be NULL. */
 int grid_dwf_cg(grid_dwf_t* h, const void* b, void* x, double tol, int maxiter, int mode, grid_dwf_cg_stats* stats);
 
-/* S = |M psi|^2 for a full field psi (FP64 or FP32), its su(3) force F and ambient gradient
+/* Source: the paper describes no derivative; this is the adjoint of the operator it profiles.
+ * Reading: with chi = M psi, the link derivative of S = |M psi|^2 comes from the hopping term
+ * alone, per link an outer product of psi and the spin-projected chi summed over s and spin;
+ * F = TA(G U^+) under U -> exp(eps A) U, TA the traceless anti-Hermitian part; FP32 fields
+ * accumulate in FP32 within blocks of 16 slices and in FP64 across blocks.
+ * S = |M psi|^2 for a full field psi (FP64 or FP32), its su(3) force F and ambient gradient
  * G = dS/dRe U + i dS/dIm U, both canonical gauge layout FP64 device buffers (either may be
  * NULL). chi: full field of the same precision receiving M psi, or NULL for handle-owned
  * scratch. Under U -> exp(eps A) U with A in su(3): dS/deps = sum Re tr(A^+ F). *S_out on host. */
@@ -181,6 +211,17 @@ int grid_dwf_force(grid_dwf_t* h, int precision, const void* psi, void* chi, dou
  * still written) if tol is not reached within maxiter. */
 int grid_dwf_pf_force(grid_dwf_t* h, const void* phi, void* X, double tol, int maxiter, int mode, int precision,
                       double* F, double* G, double* S_out, grid_dwf_cg_stats* stats);
+
+/* Measured arithmetic ceiling of the current device, the denominator of the roofline of a kernel
+ * bound by its arithmetic pipe rather than by memory (the IEEE FP64 hopping term on this GPU):
+ * FP64 FMA, scalar FP32 FMA or packed FP32x2 FMA throughput, in GFLOP/s (2 flops per FMA, 4 per
+ * packed FMA) over all SMs, the best of three timed throughput loops (independent FMA chains,
+ * 8 CTAs of 256 threads per SM) after one warm-up, on `stream` (NULL = legacy default stream).
+ * Not part of the paper's method: a measurement service (the paper's Section 3 reports its
+ * kernel's floating-point pipe utilisation, 39%, against such a ceiling). Synchronises the
+ * stream; allocates nothing. */
+enum { GRID_DWF_PEAK_FP64_FMA = 0, GRID_DWF_PEAK_FP32_FMA = 1, GRID_DWF_PEAK_FP32X2_FMA = 2 };
+int grid_dwf_pipe_peak(int kind, void* stream, double* gflops);
 
 /* |a|^2 (b == NULL) or a^+ b with FP64 accumulation, like grid_dwf_norm2 / grid_dwf_inner, for
  * callers that cannot allocate device memory: code recording a CUDA graph (where cudaMalloc is

@@ -100,6 +100,7 @@ def load(build: bool = True):
             "grid_dwf_cg": [vp, vp, vp, d, i, i, ctypes.POINTER(_CgStats)],
             "grid_dwf_force": [vp, i, vp, vp, vp, vp, dp],
             "grid_dwf_pf_force": [vp, vp, vp, d, i, i, i, vp, vp, dp, ctypes.POINTER(_CgStats)],
+            "grid_dwf_pipe_peak": [i, vp, dp],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -111,6 +112,20 @@ def load(build: bool = True):
         lib.grid_dwf_status_string.restype = ctypes.c_char_p
         _lib = lib
         return lib
+
+
+PEAK_FP64_FMA, PEAK_FP32_FMA, PEAK_FP32X2_FMA = 0, 1, 2
+
+
+def pipe_peak(kind: int) -> float:
+    """Measured FMA throughput of the current device in GFLOP/s (grid_dwf_pipe_peak): FP64,
+    scalar FP32 or packed FP32x2 fused multiply-adds over all SMs, on torch's current stream."""
+    lib = load()
+    out = ctypes.c_double(0.0)
+    rc = lib.grid_dwf_pipe_peak(int(kind), _ptr(torch.cuda.current_stream().cuda_stream), ctypes.byref(out))
+    if rc != 0:
+        raise GridDWFError(rc, "grid_dwf_pipe_peak failed")
+    return out.value
 
 
 def _ptr(t):

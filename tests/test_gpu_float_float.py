@@ -31,7 +31,12 @@ def dwf():
 
 
 def rel(a, b):
-    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+    """The larger of the relative L2 error and the largest element error relative to the largest
+    reference element (a single wrong site fails the second)."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    d = np.abs(a - b)
+    return float(max(np.linalg.norm(d) / np.linalg.norm(b), d.max() / np.abs(b).max()))
 
 
 def dev(x):
@@ -124,9 +129,9 @@ def test_m_mpc_mdagm_float_float(dwf, oracle_lib, dims, Ls):
     for dag in (False, True):
         out = host(op.unpack(op.mpc(fo, dag=dag), subset=dwf.ODD))
         ref = oracle_lib.mpc(dims, Ls, M5, MASS, BC, U, po, dag=dag)
-        assert rel(out[mask], ref[mask]) < 4 * TOL
+        assert rel(out[mask], ref[mask]) < TOL, rel(out[mask], ref[mask])
     out = host(op.unpack(op.mdagm(fo), subset=dwf.ODD))
-    assert rel(out[mask], oracle_lib.mdagm(dims, Ls, M5, MASS, BC, U, po)[mask]) < 8 * TOL
+    assert rel(out[mask], oracle_lib.mdagm(dims, Ls, M5, MASS, BC, U, po)[mask]) < TOL
 
 
 @pytest.mark.parametrize("mode", [0, 1, 2])

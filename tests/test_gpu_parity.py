@@ -1,11 +1,18 @@
 """Parity of the CUDA library (through the C ABI) with the FP64 oracle, element by element.
 
-Tolerances are relative L2 norms over the whole field, |y_gpu - y_ref| / |y_ref|:
-  FP64 1e-12; FP32 1e-5 (both from the operator's specification);
+Every comparison checks two measures against the same tolerance: the relative L2 norm over the
+whole field, |y_gpu - y_ref| / |y_ref|, and the largest element error relative to the largest
+reference element, max|y_gpu - y_ref| / max|y_ref| (a single wrong site, which moves the L2
+measure by only about 1/sqrt(sites), fails the second). Tolerances:
+  FP64 1e-12; FP32 1e-5 (both from the operator's specification), for Dhop, Mooee, M, Mpc and
+  Mpc^+ Mpc alike: every launch computes in the storage precision and these operators have no
+  cancellation that amplifies rounding (|Mpc x| is comparable to |Mooee x|);
   FP16 / BF16 storage with FP32 arithmetic, against the oracle applied to the same rounded
   inputs: the output is rounded once to the storage format (unit roundoff 2^-11 / 2^-8) after
-  FP32 arithmetic, so 2e-3 (FP16) and 1.6e-2 (BF16) bound it with margin; against the exact
-  inputs the error is reported and bounded loosely (input rounding of 24 + 18 reals per hop).
+  FP32 arithmetic, so 2e-3 (FP16) and 1.6e-2 (BF16) bound it with margin; the Schur operators
+  store their intermediate fields in the storage format too (Mpc two launches, Mpc^+ Mpc four,
+  each rounding its output once), so they get 4x and 8x that bound; against the exact inputs the
+  error is reported and bounded loosely (input rounding of 24 + 18 reals per hop).
 """
 import numpy as np
 import pytest
@@ -31,9 +38,16 @@ def dwf():
 
 
 def rel(a, b):
+    """The larger of the relative L2 error and the largest element error relative to the largest
+    reference element."""
     a = np.asarray(a)
     b = np.asarray(b)
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    d = np.abs(a - b)
+    return float(max(np.linalg.norm(d) / np.linalg.norm(b), d.max() / np.abs(b).max()))
+
+
+# Schur operators in 16-bit storage: one output rounding per launch (Mpc 2 launches, Mpc^+ Mpc 4)
+SCHUR_FACTOR = {"mpc": {0: 1, 1: 1, 2: 4, 3: 4}, "mdagm": {0: 1, 1: 1, 2: 8, 3: 8}}
 
 
 def dev(x):
@@ -134,7 +148,7 @@ def test_dhop_largest_ls(dwf, oracle_lib, prec):
     mask = oracle_lib.parity_mask(dims)
     out = host(op.unpack(op.mdagm(op.pack(dev(po), prec, dwf.ODD)), subset=dwf.ODD))
     ref = oracle_lib.mdagm(dims, Ls, M5, MASS, BC, round_spinor(U, prec), po)
-    assert rel(out[mask], ref[mask]) < 8 * TOL[prec]
+    assert rel(out[mask], ref[mask]) < SCHUR_FACTOR["mdagm"][prec] * TOL[prec]
 
 
 @pytest.mark.parametrize("prec", [2, 3])
@@ -209,10 +223,10 @@ def test_m_mpc_mdagm(dwf, oracle_lib, dims, Ls, prec):
     for dag in (False, True):
         out = host(op.unpack(op.mpc(fo, dag=dag), subset=dwf.ODD))
         ref = oracle_lib.mpc(dims, Ls, M5, MASS, BC, U_r, po, dag=dag)
-        assert rel(out[mask], ref[mask]) < 4 * TOL[prec]
+        assert rel(out[mask], ref[mask]) < SCHUR_FACTOR["mpc"][prec] * TOL[prec], (dag, rel(out[mask], ref[mask]))
     out = host(op.unpack(op.mdagm(fo), subset=dwf.ODD))
     ref = oracle_lib.mdagm(dims, Ls, M5, MASS, BC, U_r, po)
-    assert rel(out[mask], ref[mask]) < 8 * TOL[prec]
+    assert rel(out[mask], ref[mask]) < SCHUR_FACTOR["mdagm"][prec] * TOL[prec], rel(out[mask], ref[mask])
 
 
 def test_mdagm_low_precision(dwf, oracle_lib):
@@ -459,13 +473,17 @@ def test_full_size_dhop_16x16x16x16_ls16(dwf, oracle_lib, prec):
     op = dwf.GridDWF(dims, Ls, w["M5"], w["mass"], bc=BC)
     op.set_gauge(dev(U))
     f = op.pack(dev(psi), prec, dwf.FULL)
+    ref = oracle_lib.dhop(dims, Ls, BC, round_spinor(U, prec), round_spinor(psi, prec))
+    # the benchmark's launch: one full-lattice call (the packed precisions apply both halves in
+    # one launch, the second half from the CTAs past the first half's grid)
+    got = host(op.unpack(op.dhop(f, dwf.FULL)))
+    assert rel(got, ref) < TOL[prec], rel(got, ref)
+    # and the two half-lattice launches
     half = op.half_reals
     out = op.field(prec, dwf.FULL)
-    # the benchmark's launch configuration: two half-lattice applications
     op.dhop(f[half:], dwf.EVEN, out=out[:half])
     op.dhop(f[:half], dwf.ODD, out=out[half:])
     got = host(op.unpack(out))
-    ref = oracle_lib.dhop(dims, Ls, BC, round_spinor(U, prec), round_spinor(psi, prec))
     assert rel(got, ref) < TOL[prec], rel(got, ref)
 
 
@@ -568,4 +586,4 @@ def test_random_shape_sweep(dwf, oracle_lib, dims, Ls, prec):
         ref = oracle_lib.dhop(dims, Ls, BC, U_r, psi_r, dag=dag)
         assert rel(host(op.unpack(op.dhop(f, dwf.FULL, dag=dag))), ref) < TOL[prec], ("dhop", dag)
     ref = oracle_lib.m(dims, Ls, M5, MASS, BC, U_r, psi_r)
-    assert rel(host(op.unpack(op.m(f))), ref) < 2 * TOL[prec], "m"
+    assert rel(host(op.unpack(op.m(f))), ref) < TOL[prec], ("m", rel(host(op.unpack(op.m(f))), ref))
