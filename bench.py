@@ -519,9 +519,11 @@ def run_cg32(dwf, torch):
 
 
 def profile_case(args):
-    """A fixed, short launch sequence for a profiler (ncu): the full-lattice Dhop of one precision
-    on the named workload, 3 warm-up calls then 3 more, fields drawn on the device. Prints one line
-    with the CUDA-event time of the last three (a number taken under a profiler is not a result)."""
+    """A fixed, short launch sequence for a profiler (ncu), fields drawn on the device:
+    --profile-kernel dhop: the full-lattice Dhop of one precision on the named workload, 3 warm-up
+    calls then 3 more; force: the action and force (FP32 fields) likewise; cg: one mixed solve
+    (mode from --variants: f32, f16, bf16) to 1e-10. Prints one line with the CUDA-event time
+    (a number taken under a profiler is not a result)."""
     import torch
 
     from paper_2203_06777_gb300 import dwf
@@ -529,6 +531,33 @@ def profile_case(args):
     torch.cuda.set_device(0)
     spec = synth.WORKLOADS[args.profile]
     dims, Ls = spec["dims"], spec["Ls"]
+    if args.profile_kernel in ("force", "cg"):
+        dev = torch.device("cuda")
+        op = dwf.GridDWF(dims, Ls, spec["M5"], spec["mass"], bc=BC)
+        op.set_gauge(synth.random_gauge_device(dims, 1000 * spec["case"], spec["eps"] or 0.3, dev))
+        psi = synth.random_spinor_device(dims, Ls, 1000 * spec["case"] + 1, dev)
+        if args.profile_kernel == "force":
+            f = op.pack(psi, dwf.FP32, dwf.FULL)
+            chi = op.field(dwf.FP32, dwf.FULL)
+            for _ in range(3):
+                op.force(f, chi=chi)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(3):
+                op.force(f, chi=chi)
+            torch.cuda.synchronize()
+            print(json.dumps({"profile_case": args.profile, "kernel": "force",
+                              "ms_per_call": round((time.perf_counter() - t0) * 1e3 / 3, 3)}), flush=True)
+        else:
+            mode = {"f32": dwf.CG_MIXED_FP32, "f16": dwf.CG_MIXED_FP16, "bf16": dwf.CG_MIXED_BF16}[
+                args.variants.split(",")[0]]
+            b = op.pack(psi, dwf.FP64, dwf.FULL)
+            x, st = op.cg(b, tol=1e-10, maxiter=20000, mode=mode, raise_on_fail=False)
+            print(json.dumps({"profile_case": args.profile, "kernel": "cg", "seconds": round(st.seconds, 4),
+                              "iterations": st.iterations, "reliable_updates": st.reliable_updates,
+                              "true_residual": st.true_residual}), flush=True)
+        op.close()
+        return
     prec = {"f32": dwf.FP32, "f16": dwf.FP16, "bf16": dwf.BF16, "f64": dwf.FP64, "f64ff": dwf.FP64}[args.variants.split(",")[0]]
     dev = torch.device("cuda")
     op = dwf.GridDWF(dims, Ls, spec["M5"], spec["mass"], bc=BC,
@@ -763,8 +792,10 @@ def main(argv=None):
     ap.add_argument("--no-sweep", action="store_true", help="skip the 32^4 x 16 Dhop roofline sweep")
     ap.add_argument("--no-cg32", action="store_true", help="skip the 32^4 x 16 mixed vs FP64 CG (about 25 s)")
     ap.add_argument("--no-force", action="store_true", help="skip the action/force and pseudofermion force timing")
-    ap.add_argument("--profile", default=None, help="run only a short Dhop launch sequence of this workload "
+    ap.add_argument("--profile", default=None, help="run only a short launch sequence of this workload "
                     "(a synth.WORKLOADS name) for a profiler, in the first precision of --variants")
+    ap.add_argument("--profile-kernel", default="dhop", choices=["dhop", "force", "cg"],
+                    help="what --profile runs: the hopping term, the action and force, or one mixed CG solve")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

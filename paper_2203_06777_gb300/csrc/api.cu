@@ -1,6 +1,7 @@
 // C ABI of the domain-wall operator library (declared in include/grid_dwf.h): the operator
 // handle, argument checking, the fused kernel sequences of M, Mpc and Mpc^+ Mpc, and the plain
 // and mixed-precision CG solvers, driven from the host on the handle's stream.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
@@ -35,8 +36,16 @@ struct grid_dwf {
   double* partials = nullptr;           // reduction partial sums
   double* scal = nullptr;               // CG scalars (device)
   double* host_scal = nullptr;          // pinned mirror of scal
+  // CG: |r|^2 of each inner iteration copied to a pinned ring with an event, so that the host
+  // reads an iteration's residual while the next iteration is already queued
+  static constexpr int RING = 4;
+  double* host_ring = nullptr;
+  cudaEvent_t ring_ev[RING] = {};
   std::string err;
   bool sync_debug = false;
+  // walk of the packed hopping launches in z-blocks of this many planes (-1: automatic; the
+  // environment variable GRID_DWF_ZBLOCK, read at create, overrides it; 0 = lexicographic)
+  int zblk = -1;
   int fp64_arith = GRID_DWF_FP64_ARITH_NATIVE;  // arithmetic of the FP64 hopping term
 };
 
@@ -74,6 +83,15 @@ enum WsId : int {
   WS_PF_B,
   WS_PF_A32,
   WS_PF_B32,
+  WS_CG_RED,
+};
+
+// Optional CG epilogue of a packed half-lattice hop (see dhop_kernel.cuh): per-CTA partial sums
+// into red; with r, the update r -= (*coef) * result instead of a stored result.
+struct CgEpilogue {
+  double* red = nullptr;
+  float* r = nullptr;
+  const double* coef = nullptr;
 };
 
 int fail(grid_dwf_t* h, int code, const std::string& msg) {
@@ -161,9 +179,14 @@ int ensure_gauge(grid_dwf_t* h, int prec) {
 // One half-lattice hopping application with its fused epilogue.
 int dhop_half(grid_dwf_t* h, int prec, const void* in, void* out, int out_parity, bool dag, int pre, int post,
               double alpha, double beta, const void* aux, const void* in2 = nullptr, void* out2 = nullptr,
-              const void* aux2 = nullptr) {
+              const void* aux2 = nullptr, const CgEpilogue& epi = CgEpilogue()) {
   RET(ensure_gauge(h, prec));
   DhopArgs a;
+  a.red = epi.red;
+  a.r = epi.r;
+  a.axpy_coef = epi.coef;
+  a.red_base = 0;
+  a.own_from = 0;
   a.in2 = in2;
   a.out2 = out2;
   a.aux2 = aux2;
@@ -182,6 +205,24 @@ int dhop_half(grid_dwf_t* h, int prec, const void* in, void* out, int out_parity
   a.pre = pre;
   a.post = post;
   a.site_base = 0;
+  a.zblk = 0;
+  a.ctas_per_plane = 1;
+  {
+    // Automatic choice (measured at 32^4 x 16, where the FP32 half field is 805 MB: lexicographic
+    // walk 988 us, z-blocks of 2 / 4 / 8 / 16 planes 920 / 859 / 833 / 868 us; no change at 16^4,
+    // whose fields stay in L2; the 16-bit kernels, bound by their arithmetic, gain nothing): blocks
+    // of 8 planes for FP32 fields larger than about 3/4 of L2.
+    const int plane = h->g.Lxh * h->g.L[1];
+    int zb = h->zblk;
+    if (zb < 0) zb = (prec == GRID_DWF_FP32 && half_bytes(h, prec) > ((size_t)96 << 20)) ? 8 : 0;
+    if (prec != GRID_DWF_FP64 && zb > 0 && zb < h->g.L[2] && h->g.L[2] % zb == 0 && plane % a.sites_per_cta == 0) {
+      a.zblk = zb;
+      a.ctas_per_plane = plane / a.sites_per_cta;
+      a.div_cpp = make_fastdiv((uint32_t)a.ctas_per_plane);
+      a.div_zblk = make_fastdiv((uint32_t)zb);
+      a.div_lt = make_fastdiv((uint32_t)h->g.L[3]);
+    }
+  }
   a.alpha = alpha;
   a.beta = beta;
   a.d5 = h->d5;
@@ -320,10 +361,15 @@ int grid_dwf_create(const int dims[4], int Ls, double M5, double mass, const int
   h->stream = static_cast<cudaStream_t>(stream);
   const char* sd = std::getenv("GRID_DWF_SYNC_DEBUG");
   h->sync_debug = sd && sd[0] == '1';
+  const char* zbe = std::getenv("GRID_DWF_ZBLOCK");
+  if (zbe) h->zblk = std::atoi(zbe);
   cudaGetDevice(&h->device);
   cudaError_t e = cudaMalloc(&h->partials, sizeof(double) * 2 * RED_BLOCKS);
   if (e == cudaSuccess) e = cudaMalloc(&h->scal, sizeof(double) * S_COUNT);
   if (e == cudaSuccess) e = cudaMallocHost(&h->host_scal, sizeof(double) * (2 * S_COUNT + 1));
+  if (e == cudaSuccess) e = cudaMallocHost(&h->host_ring, sizeof(double) * grid_dwf::RING);
+  for (int k = 0; k < grid_dwf::RING && e == cudaSuccess; ++k)
+    e = cudaEventCreateWithFlags(&h->ring_ev[k], cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemset(h->scal, 0, sizeof(double) * S_COUNT);
   if (e != cudaSuccess) {
     grid_dwf_destroy(h);
@@ -352,6 +398,9 @@ int grid_dwf_destroy(grid_dwf_t* h) {
   cudaFree(h->partials);
   cudaFree(h->scal);
   cudaFreeHost(h->host_scal);
+  cudaFreeHost(h->host_ring);
+  for (auto& ev : h->ring_ev)
+    if (ev) cudaEventDestroy(ev);
   delete h;
   return GRID_DWF_OK;
 }
@@ -633,25 +682,66 @@ int cg_normal(grid_dwf_t* h, const void* rhs, void* xo_, double tol, int maxiter
     RET(read_scalars(h));
     double rr_s = h->host_scal[S_RR];
     double rr_max = rr_s;
+    // The normal operator's launches with the vector algebra fused (18-real links): p^+ A p is
+    // |Mpc p|^2, summed in the epilogue of Mpc's second launch, and r -= alpha A p happens in the
+    // epilogue of Mpc^+'s second launch, so A p is never stored. Partial sums: one per CTA.
+    const bool fused = !h->c12;
+    double* red = nullptr;
+    int nred = 0;
+    if (fused) {
+      const int spc = std::max(1, std::min(128 / dhop_threads_per_site(PS, Ls), (int)N));
+      nred = (int)(N / spc) + 1;
+      void* rp = nullptr;
+      RET(ws_get(h, WS_CG_RED, sizeof(double) * (size_t)nred, &rp));
+      red = static_cast<double*>(rp);
+    }
+    int last_update = 0;  // iteration of the last reliable update (its |r|^2 is on another scale)
     while (!converged && iters < maxiter) {
-      RET(mdagm_impl(h, PS, ps, aps, tos, tes));
-      CK(launch_reduce(PS, ps, aps, N, Ls, h->partials, h->scal, FIN_ALPHA, 0, h->stream), "cg pAp");
-      // r -= alpha Ap now; x += alpha p is deferred to the pass that updates p (one read of p)
-      CK(launch_cg_r(GRID_DWF_FP32, PS, rs, aps, N, Ls, h->partials, h->scal, h->stream), "cg update");
+      if (fused) {
+        CgEpilogue norm;
+        norm.red = red;
+        CgEpilogue axpy;
+        axpy.red = red;
+        axpy.r = static_cast<float*>(rs);
+        axpy.coef = h->scal + S_ALPHA;
+        RET(dhop_half(h, PS, ps, tes, 0, false, PRE_NONE, POST_INV, 1.0, 0.0, nullptr));
+        RET(dhop_half(h, PS, tes, tos, 1, false, PRE_MOOEE, POST_NONE, -0.25, 1.0, ps, nullptr, nullptr, nullptr, norm));
+        CK(launch_finalize_n(red, nred, h->scal, FIN_ALPHA, 0, h->stream), "cg pAp");
+        RET(dhop_half(h, PS, tos, tes, 0, true, PRE_NONE, POST_INV_DAG, 1.0, 0.0, nullptr));
+        RET(dhop_half(h, PS, tes, aps, 1, true, PRE_MOOEE_DAG, POST_NONE, -0.25, 1.0, tos, nullptr, nullptr, nullptr,
+                      axpy));
+        CK(launch_finalize_n(red, nred, h->scal, FIN_BETA, 0, h->stream), "cg update");
+      } else {
+        RET(mdagm_impl(h, PS, ps, aps, tos, tes));
+        CK(launch_reduce(PS, ps, aps, N, Ls, h->partials, h->scal, FIN_ALPHA, 0, h->stream), "cg pAp");
+        // r -= alpha Ap now; x += alpha p is deferred to the pass that updates p (one read of p)
+        CK(launch_cg_r(GRID_DWF_FP32, PS, rs, aps, N, Ls, h->partials, h->scal, h->stream), "cg update");
+      }
       flops += 4 * half_flops;
       ++iters;
       rr_is_true = false;  // x_s has moved since the last true residual
-      bool reliable = false;
-      RET(read_scalars(h));
-      const double rr_old_s = rr_s;  // |r_s|^2 before this step (the denominator of beta)
-      rr_s = h->host_scal[S_RRNEW];
-      if (!is_finite(rr_s)) return fail(h, GRID_DWF_ERR_NONFINITE, "cg: non-finite sloppy residual");
-      const double est = std::sqrt(rr_s) / sigma;  // estimated true-scale |r|
-      if (rr_s < delta * delta * rr_max || est <= target || iters == maxiter) {
-        // reliable update: complete x_s (the pending alpha p), fold it into x, recompute the true
-        // residual in FP64, rescale
+      // |r|^2 of this iteration to the host ring; the decision below reads the previous
+      // iteration's, which is complete or nearly so while this one is still queued
+      const int slot = iters % grid_dwf::RING;
+      CK(cudaMemcpyAsync(h->host_ring + slot, h->scal + S_RRNEW, sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+         "cg residual copy");
+      CK(cudaEventRecord(h->ring_ev[slot], h->stream), "cg residual copy");
+      bool reliable = iters == maxiter;
+      if (iters - 1 > last_update) {
+        const int prev = (iters - 1) % grid_dwf::RING;
+        CK(cudaEventSynchronize(h->ring_ev[prev]), "cg residual read");
+        const double rp = h->host_ring[prev];
+        if (!is_finite(rp)) return fail(h, GRID_DWF_ERR_NONFINITE, "cg: non-finite sloppy residual");
+        if (rp < delta * delta * rr_max || std::sqrt(rp) / sigma <= target) reliable = true;
+      }
+      if (reliable) {
+        // reliable update (one iteration after the residual that called for it): complete x_s (the
+        // pending alpha p), fold it into x, recompute the true residual in FP64, rescale
+        RET(read_scalars(h));
+        rr_s = h->host_scal[S_RRNEW];
+        const double rr_old_s = h->host_scal[S_RROLD];  // |r_s|^2 before this step (the denominator of beta)
+        if (!is_finite(rr_s)) return fail(h, GRID_DWF_ERR_NONFINITE, "cg: non-finite sloppy residual");
         CK(launch_cg_xp(GRID_DWF_FP32, PS, xs, rs, ps, N, Ls, h->scal, false, h->stream), "cg reliable");
-        reliable = true;
         RET(write_scalar(h, S_TMP0, 1.0 / sigma));
         CK(launch_accum_zero(GRID_DWF_FP32, xo, xs, N, Ls, h->scal + S_TMP0, h->stream), "cg reliable");
         RET(mdagm_impl(h, P, xo, Ap, to, te));
@@ -659,6 +749,7 @@ int cg_normal(grid_dwf_t* h, const void* rhs, void* xo_, double tol, int maxiter
         CK(launch_residual64(rhs, Ap, r, N, Ls, h->partials, h->scal, S_TMP1, h->stream), "cg reliable");
         RET(read_scalars(h));
         ++updates;
+        last_update = iters;
         const double rr64 = h->host_scal[S_TMP1];
         if (!is_finite(rr64)) return fail(h, GRID_DWF_ERR_NONFINITE, "cg: non-finite true residual");
         rr = rr64;
@@ -680,11 +771,11 @@ int cg_normal(grid_dwf_t* h, const void* rhs, void* xo_, double tol, int maxiter
         rr_max = rr_s;
         sigma = sigma_new;
         rr = rr64;
-      }
-      if (reliable)  // x is complete: p alone (with the rescaled beta)
-        CK(launch_cg_p(GRID_DWF_FP32, PS, rs, ps, N, Ls, h->scal, h->stream), "cg p");
-      else
+        if (iters == maxiter) break;
+        CK(launch_cg_p(GRID_DWF_FP32, PS, rs, ps, N, Ls, h->scal, h->stream), "cg p");  // x is complete: p alone
+      } else {
         CK(launch_cg_xp(GRID_DWF_FP32, PS, xs, rs, ps, N, Ls, h->scal, true, h->stream), "cg xp");
+      }
     }
   }
   // final true residual of the normal equations, FP64 (already known when the loop ended on a

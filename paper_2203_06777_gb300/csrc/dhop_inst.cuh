@@ -21,15 +21,21 @@ static cudaError_t launch_one(const DhopArgs& a, int threads, int blocks, size_t
     // full CTAs only (the packed kernel has no tail handling); a ragged end gets one more CTA (per
     // half) flush with the end of the lattice, launched after the first so no two writes overlap
     // in time. a.in2 != nullptr: both halves of a full-lattice hop in the same launches.
+    // CG epilogues: partial sums [0, full) from the full CTAs, [full] from the end CTA, which adds
+    // only the sites the full CTAs did not cover.
     const int full = a.g.N4h / a.sites_per_cta;
     const int halves = a.in2 ? 2 : 1;
     DhopArgs m = a;
     m.blocks1 = full;
+    m.red_base = 0;
+    m.own_from = 0;
     if (full > 0) kern<<<halves * full, threads, smem, stream>>>(m);
     if (full * a.sites_per_cta != a.g.N4h) {
       DhopArgs t = a;
       t.site_base = a.g.N4h - a.sites_per_cta;
       t.blocks1 = 1;
+      t.red_base = full;
+      t.own_from = full * a.sites_per_cta;
       kern<<<halves, threads, smem, stream>>>(t);
     }
   }
@@ -45,7 +51,15 @@ static cudaError_t launch_ls(const DhopArgs& a, bool dag, bool c12, int threads,
     return c12 ? launch_one<false, true, LSC, EPI_BOTH>(a, threads, blocks, smem, stream)
                : launch_one<false, false, LSC, EPI_BOTH>(a, threads, blocks, smem, stream);
   } else {
-    // the instantiation with exactly the epilogue parts this launch uses
+    // the instantiation with exactly the epilogue parts this launch uses; the CG epilogues exist
+    // for the launches that use them only: Mpc's second launch (pre-operation Mooee, no dag) with
+    // the norm, Mpc^+'s second launch (Mooee^+, dag) with the update, 18-real links
+    if (a.red && !c12 && a.pre != PRE_NONE && a.post == POST_NONE) {
+      if (a.r && dag) return launch_one<true, false, LSC, EPI_PRE | EPI_AXPY>(a, threads, blocks, smem, stream);
+      if (!a.r && !dag) return launch_one<false, false, LSC, EPI_PRE | EPI_NORM>(a, threads, blocks, smem, stream);
+      return cudaErrorInvalidValue;
+    }
+    if (a.red) return cudaErrorInvalidValue;
     const int ek = (a.pre != PRE_NONE ? EPI_PRE : 0) | (a.post != POST_NONE ? EPI_POST : 0);
 #define DWF_EK(K)                                                                             \
   case K:                                                                                     \

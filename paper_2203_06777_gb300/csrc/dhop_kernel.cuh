@@ -54,6 +54,22 @@ struct DhopArgs {
   const void* in2;
   void* out2;
   const void* aux2;
+  // CG epilogues of the packed kernels (EPI_NORM, EPI_AXPY; one half per launch): FP64 partial
+  // sums, one per CTA, go to red[red_base + CTA index]; a thread adds nothing (and, for EPI_AXPY,
+  // stores nothing) for a site below own_from, which a previous launch already covered.
+  double* red;
+  int red_base;
+  int own_from;
+  float* r;            // EPI_AXPY: FP32 half field updated in place, r -= (*axpy_coef) * (hopping result)
+  const double* axpy_coef;
+  // Order in which the CTAs of a packed launch walk the lattice. zblk = 0: lexicographic (CTA b
+  // covers cb sites b * sites_per_cta ..). zblk > 0: the (x, y) planes are taken z-fastest within
+  // blocks of zblk planes in z, then t, then the next block in z, so that an input plane is
+  // reused by the output planes at t - 1, t, t + 1 within about 2 * zblk planes of traffic rather
+  // than 2 * Lz (L2 then holds the t-neighbours of lattices whose half field is larger than it).
+  // Requires full CTAs tiling each (x, y) plane: ctas_per_plane * sites_per_cta = Lx/2 * Ly.
+  int zblk, ctas_per_plane;
+  FastDiv div_cpp, div_zblk, div_lt;
   double alpha, beta;
   double d5;       // 5 - M5
   double mass;     // m
@@ -666,7 +682,31 @@ __device__ __forceinline__ void mooee_inv_line(R* v, int Ls, bool forward_form, 
 // Epilogue kinds compiled into a packed kernel: bit 0 the pre-operation (aux, Mooee aux, Mooee^+
 // aux), bit 1 the post-operation (Mooee^-1, (Mooee^+)^-1). A launch runs the instantiation with
 // exactly the parts it uses, so plain hops and single-epilogue hops keep fewer live registers.
-enum EpiKind : int { EPI_NONE = 0, EPI_PRE = 1, EPI_POST = 2, EPI_BOTH = 3 };
+//
+// Two more bits serve the mixed-precision CG, which needs of Mpc^+ Mpc p only two numbers and one
+// vector update (the Schur normal operator's launches 2 and 4, with their pre-operations):
+//   EPI_NORM (4): store the result as usual and add |result|^2 (the squared norm of Mpc p, which
+//                 equals p^+ Mpc^+ Mpc p) to the launch's per-CTA partial sums;
+//   EPI_AXPY (8): do not store the result; update the FP32 field r -= c * result with c read from
+//                 device memory (the CG step length), and add |r|^2 to the partial sums.
+// Neither is combined with a post-operation or with a full-lattice launch.
+enum EpiKind : int { EPI_NONE = 0, EPI_PRE = 1, EPI_POST = 2, EPI_BOTH = 3, EPI_NORM = 4, EPI_AXPY = 8 };
+
+// Sum of one value per thread over the CTA in a fixed order (warp shuffles, then the warps in
+// order), written by thread 0 to *dst.
+__device__ __forceinline__ void cta_sum_to(double v, double* dst) {
+  __shared__ double wsum[32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) wsum[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += wsum[w];
+    *dst = t;
+  }
+}
 
 // FP32 / FP16 / BF16: one thread per (site, slice pair), packed two-wide arithmetic.
 template <int P, bool DAG, bool C12, int LSC, int EK>
@@ -688,7 +728,17 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
   const bool second = (int)blockIdx.x >= a.blocks1;  // the other half of a full-lattice launch
   const int bid = second ? (int)blockIdx.x - a.blocks1 : (int)blockIdx.x;
   const int out_parity = second ? 1 - a.out_parity : a.out_parity;
-  const int site = a.site_base + bid * a.sites_per_cta + site_local;
+  int cta = bid;
+  if (a.zblk > 0) {  // plane w = zi + zblk * (t + Lt * zb) of the walk is the lattice's plane z + Lz * t
+    const uint32_t w = fdiv((uint32_t)bid, a.div_cpp);
+    const int in_plane = bid - (int)w * a.ctas_per_plane;
+    const uint32_t r = fdiv(w, a.div_zblk);
+    const int zi = (int)(w - r * (uint32_t)a.zblk);
+    const uint32_t zb = fdiv(r, a.div_lt);
+    const int t = (int)(r - zb * (uint32_t)a.g.L[3]);
+    cta = in_plane + a.ctas_per_plane * ((int)zb * a.zblk + zi + a.g.L[2] * t);
+  }
+  const int site = a.site_base + cta * a.sites_per_cta + site_local;
   constexpr bool active = true;
   const size_t site_bytes = (size_t)Lsh * 2 * 24 * sizeof(T);
   const float alpha = (float)a.alpha;
@@ -811,11 +861,32 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
   }
   const bool pad_lane = (Ls & 1) && q == Lsh - 1;  // slice 2q+1 is the zero pad
   if (!(EK & EPI_POST) || a.post == POST_NONE) {
-    if (active) {
-      if (pad_lane) {
+    if (pad_lane) {
 #pragma unroll
-        for (int r = 0; r < 24; ++r) acc[r].y = 0.f;
+      for (int r = 0; r < 24; ++r) acc[r].y = 0.f;
+    }
+    if constexpr ((EK & (EPI_NORM | EPI_AXPY)) != 0) {
+      const bool owned = site >= a.own_from;
+      float n2 = 0.f;
+      if constexpr ((EK & EPI_AXPY) != 0) {
+        // r -= c * result (FP32 field, the same site blocks with FP32 vectors)
+        char* rb = reinterpret_cast<char*>(a.r) + site_offset(site, Lsh, (size_t)Lsh * 2 * 24 * sizeof(float));
+        float2 rv[24];
+        load_pair<P32, LSHC>(rb, q, Lsh, rv);
+        const float2 MC = f2(-(float)*a.axpy_coef);
+#pragma unroll
+        for (int r = 0; r < 24; ++r) {
+          rv[r] = ffma2(MC, acc[r], rv[r]);
+          n2 = fmaf(rv[r].x, rv[r].x, fmaf(rv[r].y, rv[r].y, n2));
+        }
+        if (owned) store_pair<P32, LSHC>(rb, q, Lsh, rv);
+      } else {
+        store_pair<P, LSHC>(outb, q, Lsh, acc);
+#pragma unroll
+        for (int r = 0; r < 24; ++r) n2 = fmaf(acc[r].x, acc[r].x, fmaf(acc[r].y, acc[r].y, n2));
       }
+      cta_sum_to(owned ? (double)n2 : 0.0, a.red + a.red_base + bid);
+    } else {
       store_pair<P, LSHC>(outb, q, Lsh, acc);
     }
     return;

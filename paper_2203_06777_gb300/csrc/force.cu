@@ -242,6 +242,184 @@ __global__ void __launch_bounds__(128) k_force(const Geom g, const char* psi, co
   }
 }
 
+// FP32 fields with 8 or 16 slice pairs per site (Ls 15-16, 31-32; the static shared memory of
+// fewer pairs per site, i.e. more sites per CTA, would pass 48 KB): a site's
+// threads are LSH consecutive lanes of one warp, so the sums over its slices run in registers and
+// every synchronisation is within a warp.
+//   - Each field is read once as the own site's spinor: the B1 products of all four directions
+//     first (own chi(x) held in registers, psi(x + mu) loaded per direction), then the B2 products
+//     (own psi(x) held, chi(x + mu) loaded): 10 spinor loads per (site, pair) instead of 16.
+//   - The 9 complex products of one (direction, term) are summed over the site's lanes by a
+//     butterfly reduce-scatter (xor shuffles; at each level a lane keeps one half of its values
+//     and adds its partner's copy of that half), after which lane q holds entries
+//     q * NPAD / LSH .. of the site's sum; those go to shared memory.
+//   - The link algebra of the site's four links (36 entries) is spread over the same lanes.
+// Rounding: the products of a slice pair and the sums over at most 16 pairs are FP32, as in the
+// general kernel (which flushes to FP64 after 8 pairs; here 16 pairs at most are summed in FP32).
+template <int LSH>
+struct ForceRegGeom {
+  static constexpr int SPC = 128 / LSH;                             // sites per CTA
+  static constexpr int PER_LANE = (18 + LSH - 1) / LSH;              // sum entries per lane after reduce-scatter
+  static constexpr int NPAD = PER_LANE * LSH;                         // 18 reals padded to a multiple of LSH
+  // B1 B2 per mu, U per mu, Y per mu, plus one float so that sites start in different banks
+  static constexpr int SITE_FLOATS = 4 * 36 + 4 * 18 + 4 * 18 + 1;
+};
+
+template <int N, int LSH>
+__device__ __forceinline__ void reduce_scatter(float (&v)[N], int lane_in_site) {
+  // levels with partner offsets LSH/2, ..., 1: keep the half selected by the offset's bit
+#pragma unroll
+  for (int off = LSH / 2, len = N / 2; off >= 1; off >>= 1, len >>= 1) {
+    const bool upper = (lane_in_site & off) != 0;
+#pragma unroll
+    for (int k = 0; k < len; ++k) {
+      const float send = upper ? v[k] : v[len + k];
+      const float keep = upper ? v[len + k] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+}
+
+template <bool C12, int LSH>
+__global__ void __launch_bounds__(128, 4) k_force_reg(const Geom g, const char* psi, const char* chi, const char* Ue,
+                                                      const char* Uo, double* F, double* G, double coef) {
+  using GG = ForceRegGeom<LSH>;
+  constexpr int LB = link_bytes(4, C12);
+  constexpr int SPC = GG::SPC, NPAD = GG::NPAD, PER_LANE = GG::PER_LANE;
+  const size_t site_bytes = (size_t)LSH * 2 * 24 * 4;
+  const size_t half_bytes = (size_t)g.N4h * site_bytes;
+  const int p = blockIdx.x & 1;
+  const int first = (blockIdx.x >> 1) * SPC;
+  const int tid = threadIdx.x;
+  const int site_local = tid / LSH;
+  const int q = tid - site_local * LSH;  // slice pair, and the lane's place in its site's group
+  const bool active = first + site_local < g.N4h;
+  const int i = active ? first + site_local : first;  // inactive lanes compute a valid site, store nothing
+  int c[4];
+  cb_coords(g, i, p, c);
+  int nbr[4], phs[4];
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) nbr[mu] = cb_neighbour(g, i, c, mu, true, phs[mu]);
+
+  __shared__ float ssm[SPC][GG::SITE_FLOATS];
+  // the own site's spinor of the current term, one 16-byte vector per (chunk, thread): read back
+  // for each direction's projection instead of being held in 48 registers
+  __shared__ float4 own_sm[12][128];
+  float* bs = ssm[site_local];          // [mu][term][18]
+  float* us = bs + 4 * 36;              // [mu][18]
+  float* ys = us + 4 * 18;              // [mu][18]
+
+  // the site's four links U_mu(x), one per lane (and the third row rebuilt for 12-real links)
+  for (int mu = q; mu < 4; mu += LSH) {
+    float ur[18];
+    load_link<P32, C12>((p ? Uo : Ue) + ((size_t)i * 4 + mu) * LB, ur);
+#pragma unroll
+    for (int k = 0; k < 18; ++k) us[mu * 18 + k] = ur[k];
+  }
+
+#pragma unroll
+  for (int term = 0; term < 2; ++term) {
+    // term 0: B1 = sum psi(x+mu) (x) [(1 - gamma) chi(x)]^+  (own chi, projector sign -1)
+    // term 1: B2 = sum psi(x) (x) [(1 + gamma) chi(x+mu)]^+  (own psi, projector sign +1)
+    {
+      const char* ob = (term == 0 ? chi : psi) + p * half_bytes + site_offset(i, LSH, site_bytes) + (size_t)q * 16;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) own_sm[k][tid] = __ldg(reinterpret_cast<const float4*>(ob + k * chunk_stride(LSH)));
+    }
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      float2 v[24], ha[12], hb[12];
+      load_pair<P32, LSH>((term == 0 ? psi : chi) + (1 - p) * half_bytes + site_offset(nbr[mu], LSH, site_bytes), q,
+                          LSH, v);
+      {
+        float2 own[24];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          const float4 t = own_sm[k][tid];
+          own[2 * k] = make_float2(t.x, t.y);
+          own[2 * k + 1] = make_float2(t.z, t.w);
+        }
+        if (term == 0)
+          project2<-1>(mu, own, hb);
+        else
+          project2<+1>(mu, own, ha);
+      }
+      if (term == 0)
+        project2<-1>(mu, v, ha);
+      else
+        project2<+1>(mu, v, hb);
+      float s[NPAD];
+#pragma unroll
+      for (int k = 18; k < NPAD; ++k) s[k] = 0.f;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {  // sum_h ha[h][a] conj(hb[h][b]), both slices of the pair
+          float2 re = make_float2(0.f, 0.f), im = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const float2 xr = ha[(h * 3 + a) * 2], xi = ha[(h * 3 + a) * 2 + 1];
+            const float2 yr = hb[(h * 3 + b) * 2], yi = hb[(h * 3 + b) * 2 + 1];
+            re = ffma2(xr, yr, ffma2(xi, yi, re));
+            im = ffma2(xi, yr, ffma2(make_float2(-xr.x, -xr.y), yi, im));
+          }
+          s[(a * 3 + b) * 2] = re.x + re.y;
+          s[(a * 3 + b) * 2 + 1] = im.x + im.y;
+        }
+      reduce_scatter<NPAD, LSH>(s, q);
+#pragma unroll
+      for (int k = 0; k < PER_LANE; ++k) {
+        const int e = q * PER_LANE + k;
+        if (e < 18) bs[mu * 36 + term * 18 + e] = s[k];
+      }
+    }
+  }
+  __syncwarp();
+  // link algebra, one (mu, a, b) entry per task over the site's lanes:
+  //   G[a][b] = -phase (conj(B1[b][a]) + B2[a][b]),  Y = phase (-U B1 + B2 U^+)
+  const long lex = c[0] + (long)g.L[0] * (c[1] + (long)g.L[1] * (c[2] + (long)g.L[2] * c[3]));
+  for (int task = q; task < 36; task += LSH) {
+    const int mu = task / 9, ab = task - mu * 9, a = ab / 3, b = ab - a * 3;
+    const int ph = mu == 0 ? phs[0] : mu == 1 ? phs[1] : mu == 2 ? phs[2] : phs[3];
+    const float phd = (float)(coef * (double)ph);
+    const float* B1 = bs + mu * 36;
+    const float* B2 = B1 + 18;
+    const float* ur = us + mu * 18;
+    float yr = 0.f, yi = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float ar = ur[(a * 3 + k) * 2], ai = ur[(a * 3 + k) * 2 + 1];
+      const float br = B1[(k * 3 + b) * 2], bi = B1[(k * 3 + b) * 2 + 1];
+      yr -= ar * br - ai * bi;
+      yi -= ar * bi + ai * br;
+      const float cr = B2[(a * 3 + k) * 2], ci = B2[(a * 3 + k) * 2 + 1];
+      const float dr = ur[(b * 3 + k) * 2], di = -ur[(b * 3 + k) * 2 + 1];  // (U^+)[k][b] = conj(U[b][k])
+      yr += cr * dr - ci * di;
+      yi += cr * di + ci * dr;
+    }
+    ys[mu * 18 + ab * 2] = phd * yr;
+    ys[mu * 18 + ab * 2 + 1] = phd * yi;
+    if (G && active) {
+      const double gr = (double)(-phd * (B1[(b * 3 + a) * 2] + B2[ab * 2]));
+      const double gi = (double)(-phd * (-B1[(b * 3 + a) * 2 + 1] + B2[ab * 2 + 1]));
+      *reinterpret_cast<double2*>(G + (lex * 4 + mu) * 18 + ab * 2) = make_double2(gr, gi);
+    }
+  }
+  __syncwarp();
+  // F = -TA(Y): TA(Y)[a][b] = (Y[a][b] - conj(Y[b][a]))/2 - delta_ab tr(Y - Y^+)/6
+  if (F && active) {
+    for (int task = q; task < 36; task += LSH) {
+      const int mu = task / 9, ab = task - mu * 9, a = ab / 3, b = ab - a * 3;
+      const float* Y = ys + mu * 18;
+      const float trim = Y[1] + Y[9] + Y[17];  // Im tr Y; tr(Y - Y^+) = 2 i Im tr Y
+      const float tr_ = 0.5f * (Y[(a * 3 + b) * 2] - Y[(b * 3 + a) * 2]);
+      float ti_ = 0.5f * (Y[(a * 3 + b) * 2 + 1] + Y[(b * 3 + a) * 2 + 1]);
+      if (a == b) ti_ -= trim / 3.f;
+      *reinterpret_cast<double2*>(F + (lex * 4 + mu) * 18 + ab * 2) = make_double2(-(double)tr_, -(double)ti_);
+    }
+  }
+}
+
 // FP64 fields in float-float arithmetic (the handle's FP64 arithmetic set to float-float): the
 // per-slice products in pairs of FP32 numbers, the slice sums in float-float, then the site's
 // sums rounded to FP64 for the (per 4D site, cheap) link algebra. One thread per (site, slice)
@@ -361,6 +539,20 @@ cudaError_t launch_force(int prec, bool c12, const Geom& g, const void* psi, con
       k_force_ff<true><<<grid, threads, smem, st>>>(g, ps, ch, e, o, F, G, coef, nsg, spc);
     else
       k_force_ff<false><<<grid, threads, smem, st>>>(g, ps, ch, e, o, F, G, coef, nsg, spc);
+    return cudaGetLastError();
+  }
+  const int Lsh = ls_half(g.Ls);
+  if (prec == P32 && (Lsh == 8 || Lsh == 16)) {
+#define FR(L_)                                                                                           \
+  {                                                                                                      \
+    const dim3 gr((unsigned)(2 * ((g.N4h + ForceRegGeom<L_>::SPC - 1) / ForceRegGeom<L_>::SPC)));        \
+    if (c12)                                                                                             \
+      k_force_reg<true, L_><<<gr, 128, 0, st>>>(g, ps, ch, e, o, F, G, coef);                            \
+    else                                                                                                 \
+      k_force_reg<false, L_><<<gr, 128, 0, st>>>(g, ps, ch, e, o, F, G, coef);                           \
+  }
+    if (Lsh == 8) FR(8) else FR(16)
+#undef FR
     return cudaGetLastError();
   }
   switch (prec) {

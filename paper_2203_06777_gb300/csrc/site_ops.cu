@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_finalize(const double* partials
     } else if (kind == FIN_BETA) {
       scal[S_RRNEW] = tot;
       scal[S_BETA] = scal[S_PSCALE] * tot / scal[S_RR];
+      scal[S_RROLD] = scal[S_RR];
       scal[S_RR] = tot;
       scal[S_PSCALE] = 1.0;
     }
@@ -126,6 +127,40 @@ __global__ void __launch_bounds__(RED_THREADS) k_finalize(const double* partials
 
 static cudaError_t finalize(const double* partials, int ncomp, double* scal, int kind, int dst, cudaStream_t st) {
   k_finalize<<<1, RED_THREADS, 0, st>>>(partials, ncomp, scal, kind, dst);
+  return cudaGetLastError();
+}
+
+// n partials (any n) summed in a fixed order: thread t takes t, t + RED_THREADS, ..., then a tree.
+__global__ void __launch_bounds__(RED_THREADS) k_finalize_n(const double* partials, int n, double* scal, int kind,
+                                                           int dst) {
+  __shared__ double red[RED_THREADS];
+  double t = 0;
+  for (int i = threadIdx.x; i < n; i += RED_THREADS) t += partials[i];
+  red[threadIdx.x] = t;
+  __syncthreads();
+  for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double tot = red[0];
+    if (kind == FIN_STORE) {
+      scal[dst] = tot;
+    } else if (kind == FIN_ALPHA) {
+      scal[S_PAP] = tot;
+      scal[S_ALPHA] = scal[S_RR] / tot;
+    } else if (kind == FIN_BETA) {
+      scal[S_RRNEW] = tot;
+      scal[S_BETA] = scal[S_PSCALE] * tot / scal[S_RR];
+      scal[S_RROLD] = scal[S_RR];
+      scal[S_RR] = tot;
+      scal[S_PSCALE] = 1.0;
+    }
+  }
+}
+
+cudaError_t launch_finalize_n(const double* partials, int n, double* scal, int kind, int dst, cudaStream_t st) {
+  k_finalize_n<<<1, RED_THREADS, 0, st>>>(partials, n, scal, kind, dst);
   return cudaGetLastError();
 }
 

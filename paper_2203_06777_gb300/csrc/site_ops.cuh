@@ -18,6 +18,7 @@ enum CgScalar : int {
   S_PSCALE = 5, // factor applied to p in the next p update (rescaling of the sloppy vectors)
   S_TMP0 = 6,
   S_TMP1 = 7,
+  S_RROLD = 8,  // |r|^2 before the last FIN_BETA (the denominator of its beta)
   S_COUNT = 16
 };
 
@@ -30,8 +31,13 @@ constexpr int RED_THREADS = 256;
 enum FinalKind : int {
   FIN_STORE = 0,  // scal[dst] = total (and scal[dst+1] = imaginary part for inner products)
   FIN_ALPHA = 1,  // scal[S_PAP] = total; scal[S_ALPHA] = scal[S_RR] / total
-  FIN_BETA = 2,   // scal[S_RRNEW] = total; scal[S_BETA] = scal[S_PSCALE] * total / scal[S_RR]; scal[S_RR] = total
+  FIN_BETA = 2,   // scal[S_RRNEW] = total; scal[S_BETA] = scal[S_PSCALE] * total / scal[S_RR];
+                  // scal[S_RROLD] = scal[S_RR]; scal[S_RR] = total
 };
+
+// Second pass over n partial sums (one component) in a fixed order, finalised as `kind`: for the
+// per-CTA sums of the hopping kernel's CG epilogues.
+cudaError_t launch_finalize_n(const double* partials, int n, double* scal, int kind, int dst, cudaStream_t st);
 
 cudaError_t launch_pack_spinor(int prec, const Geom& g, const double* canon, void* field, int subset, bool unpack,
                                cudaStream_t st);
