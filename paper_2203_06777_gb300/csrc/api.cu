@@ -690,7 +690,7 @@ int cg_normal(grid_dwf_t* h, const void* rhs, void* xo_, double tol, int maxiter
     int nred = 0;
     if (fused) {
       const int spc = std::max(1, std::min(128 / dhop_threads_per_site(PS, Ls), (int)N));
-      nred = (int)(N / spc) + 1;
+      nred = (int)(N / spc) + (N % spc ? 1 : 0);  // the full CTAs, and the end CTA if there is one
       void* rp = nullptr;
       RET(ws_get(h, WS_CG_RED, sizeof(double) * (size_t)nred, &rp));
       red = static_cast<double*>(rp);
