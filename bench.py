@@ -641,7 +641,8 @@ def gpu_arm(args):
                 # 1 ms) would see no sample, so the same step runs untimed for ~0.3 s first (clocks at
                 # their loaded value) and the sampler's window brackets that soak and the timed region.
                 cs.wait_first_sample()
-                soak(dwf, torch, sets, 0.3)
+                if not args.no_clock_soak:
+                    soak(dwf, torch, sets, 0.3)
                 secs = time_dhop(dwf, torch, sets, steps, args.warmup, world)
                 cs.wait_next_sample()
             clocks = cs.summary()
@@ -791,6 +792,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-sweep", action="store_true", help="skip the 32^4 x 16 Dhop roofline sweep")
     ap.add_argument("--no-cg32", action="store_true", help="skip the 32^4 x 16 mixed vs FP64 CG (about 25 s)")
+    ap.add_argument("--no-clock-soak", action="store_true",
+                    help="skip the untimed 0.3 s run of the step before the FP32 timing (a fixed launch count, for ncu)")
     ap.add_argument("--no-force", action="store_true", help="skip the action/force and pseudofermion force timing")
     ap.add_argument("--profile", default=None, help="run only a short launch sequence of this workload "
                     "(a synth.WORKLOADS name) for a profiler, in the first precision of --variants")
