@@ -67,6 +67,7 @@ def pipe_peaks(dwf):
 KERNEL_SOURCES = ["paper_2203_06777_gb300/csrc/dhop_kernel.cuh", "paper_2203_06777_gb300/csrc/dhop_inst.cuh",
                   "paper_2203_06777_gb300/csrc/dwf_common.cuh", "paper_2203_06777_gb300/csrc/dhop_p32.cu"]
 TRAFFIC_PROFILE = "profiles/dhop_fp32_16x16x16x16_ls16.md"
+TRAFFIC_PROFILE_32 = "profiles/dhop_fp32_32x32x32x32_ls16.md"
 
 
 def kernel_source_hash() -> str:
@@ -79,11 +80,11 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic():
-    """DRAM bytes per launch of the FP32 Dhop kernel from the committed ncu summary, if that
+def measured_traffic(profile=TRAFFIC_PROFILE):
+    """DRAM bytes per launch of the FP32 Dhop kernel from a committed ncu summary, if that
     capture was taken of the kernel sources as they are now; otherwise None."""
     try:
-        text = open(os.path.join(ROOT, TRAFFIC_PROFILE)).read()
+        text = open(os.path.join(ROOT, profile)).read()
     except OSError:
         return None
     fields = dict(line.split(":", 1) for line in text.splitlines() if line.startswith(("traffic_bytes_per_launch:",
@@ -724,7 +725,7 @@ def gpu_arm(args):
         f32 = sw["f32"]
         line["roofline_32x32x32x32_ls16"] = {
             "bound": "hbm", "achieved": f32["algorithmic_gbs"], "peak": hbm_peak, "unit": "GB/s",
-            "frac": f32["hbm_frac"], "traffic": None, "peak_kind": peak_kind,
+            "frac": f32["hbm_frac"], "traffic": measured_traffic(TRAFFIC_PROFILE_32), "peak_kind": peak_kind,
             "kernel": "dhop_kernel<FP32> (DhopEO + DhopOE in one launch)", "gflops": f32["gflops"],
             "bytes_per_launch": algorithmic_bytes_per_site(4, 16) * 2 * (32 ** 4 // 2) * 16,
             "us_per_launch": round(2 * f32["us_per_half_lattice"], 2), "steps": sw["steps"]}

@@ -587,3 +587,45 @@ def test_random_shape_sweep(dwf, oracle_lib, dims, Ls, prec):
         assert rel(host(op.unpack(op.dhop(f, dwf.FULL, dag=dag))), ref) < TOL[prec], ("dhop", dag)
     ref = oracle_lib.m(dims, Ls, M5, MASS, BC, U_r, psi_r)
     assert rel(host(op.unpack(op.m(f))), ref) < TOL[prec], ("m", rel(host(op.unpack(op.m(f))), ref))
+
+
+# ---------------------------------------------------------------- walk order and solver paths
+
+
+@pytest.mark.parametrize("zblk", [0, 2, 4])
+@pytest.mark.parametrize("prec", [1, 2])
+def test_dhop_z_blocked_walk(dwf, oracle_lib, monkeypatch, zblk, prec):
+    """The z-blocked CTA walk (chosen automatically for FP32 fields larger than L2; forced here on
+    a small lattice through GRID_DWF_ZBLOCK, read when the handle is created) visits every site
+    once: Dhop, M and Mpc^+ Mpc equal the oracle's, and the walk does not change a single bit."""
+    dims, Ls = (8, 4, 8, 6), 16
+    monkeypatch.setenv("GRID_DWF_ZBLOCK", str(zblk))
+    op, U = make(dwf, dims, Ls, 311, eps=0.3)
+    monkeypatch.setenv("GRID_DWF_ZBLOCK", "0")
+    ref_op, _ = make(dwf, dims, Ls, 311, eps=0.3)
+    psi = synth.random_spinor(dims, Ls, seed=312)
+    f = op.pack(dev(psi), prec, dwf.FULL)
+    psi_r, U_r = round_spinor(psi, prec), round_spinor(U, prec)
+    for dag in (False, True):
+        out = op.dhop(f, dwf.FULL, dag=dag)
+        assert rel(host(op.unpack(out)), oracle_lib.dhop(dims, Ls, BC, U_r, psi_r, dag=dag)) < TOL[prec]
+        assert torch.equal(out, ref_op.dhop(f, dwf.FULL, dag=dag))
+    assert torch.equal(op.m(f), ref_op.m(f))
+    _, po = parity_fields(oracle_lib, dims, psi_r)
+    fo = op.pack(dev(po), prec, dwf.ODD)
+    assert torch.equal(op.mdagm(fo), ref_op.mdagm(fo))
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3])
+def test_mixed_cg_with_compressed_links(dwf, oracle_lib, mode):
+    """12-real links take the unfused inner step (separate p^+ A p and r update passes); the
+    solution still meets the tolerance, checked by the oracle."""
+    dims, Ls = (4, 4, 4, 4), 8
+    op, U = make(dwf, dims, Ls, 93, eps=0.4, compress12=True)
+    b = synth.random_spinor(dims, Ls, seed=94)
+    fb = op.pack(dev(b), 0, dwf.FULL)
+    x, st = op.cg(fb, tol=1e-10, maxiter=5000, mode=mode)
+    assert st.converged and st.true_residual <= 1e-10
+    xs = host(op.unpack(x))
+    r = b - oracle_lib.m(dims, Ls, M5, MASS, BC, U, xs)
+    assert np.linalg.norm(r) / np.linalg.norm(b) < 1e-8
