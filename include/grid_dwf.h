@@ -223,6 +223,62 @@ int grid_dwf_pf_force(grid_dwf_t* h, const void* phi, void* X, double tol, int m
 enum { GRID_DWF_PEAK_FP64_FMA = 0, GRID_DWF_PEAK_FP32_FMA = 1, GRID_DWF_PEAK_FP32X2_FMA = 2 };
 int grid_dwf_pipe_peak(int kind, void* stream, double* gflops);
 
+/* Software-managed device cache of host fields, for workloads whose fields do not all fit in the
+ * GPU's memory. Source: the paper's Section 2.3 ("Memory models and software managed cache"):
+ * host data moved to the device when a view is opened with an access intent, a device footprint
+ * capped by a high watermark, least-recently-used replacement under the program's control, and an
+ * "advise" priority for large, rarely used fields. The cache is independent of the operator
+ * handle: a caller opens views on its host fields and passes the returned device pointers to the
+ * operator calls (which must complete, on the cache's stream or after it, before the view's data
+ * is evicted: close views only when the kernels that use them are queued behind later cache
+ * traffic on the same stream, or synchronise).
+ *   create   high_watermark: the most device bytes the cache may hold; stream: cudaStream_t of its
+ *            copies (NULL = legacy default stream); backend: NULL for CUDA (cudaMalloc, cudaFree,
+ *            cudaMemcpyAsync; host buffers should be pinned), or caller functions (each returns 0
+ *            on success) that move data, e.g. to exercise the cache without a GPU.
+ *   open     the field is the host buffer `host` of `bytes` bytes (registered on first open; the
+ *            same size on every open). Intents: GRID_DWF_ACC_READ (device copy made current),
+ *            GRID_DWF_ACC_WRITE (made current, then marked newer than the host's),
+ *            GRID_DWF_ACC_WRITE_DISCARD (device buffer provided, not filled, marked newer),
+ *            GRID_DWF_CPU_READ (host copy made current; *ptr = host), GRID_DWF_CPU_WRITE (host copy
+ *            made current and marked newer). An accelerator open returns the device pointer and
+ *            pins it until the matching close; if the new device buffer does not fit under the
+ *            watermark, unpinned fields are evicted from the back of the LRU order (fields advised
+ *            GRID_DWF_ADVISE_INFREQUENT first), a newer device copy written back before it is freed;
+ *            GRID_DWF_ERR_OOM if pinned fields leave no room. A CPU open while accelerator views
+ *            are open is GRID_DWF_ERR_ALIAS. CPU opens synchronise the cache's stream.
+ *   flush    writes every newer, unpinned device copy back to the host (the copies stay).
+ *   forget   writes back and drops one field's entry and device buffer.
+ *   query    the entry's state (0 empty: no device copy, 1 consistent, 2 host newer, 3 device
+ *            newer), its open accelerator views and device pointer (for tests and tools). */
+typedef struct grid_dwf_cache grid_dwf_cache_t;
+enum { GRID_DWF_CPU_READ = 0, GRID_DWF_CPU_WRITE = 1, GRID_DWF_ACC_READ = 2, GRID_DWF_ACC_WRITE = 3,
+       GRID_DWF_ACC_WRITE_DISCARD = 4 };
+enum { GRID_DWF_ADVISE_NORMAL = 0, GRID_DWF_ADVISE_INFREQUENT = 1 };
+typedef struct {
+  void* ctx;
+  int (*alloc)(void* ctx, size_t bytes, void** dev);
+  int (*free)(void* ctx, void* dev);
+  int (*to_device)(void* ctx, void* dev, const void* host, size_t bytes);
+  int (*to_host)(void* ctx, void* host, const void* dev, size_t bytes);
+} grid_dwf_cache_backend;
+typedef struct {
+  unsigned long long hits, misses, evictions, cpu_opens;
+  unsigned long long copies_to_device, copies_to_host, bytes_to_device, bytes_to_host;
+  size_t peak_resident, resident_bytes;
+} grid_dwf_cache_stats;
+int grid_dwf_cache_create(size_t high_watermark, void* stream, const grid_dwf_cache_backend* backend,
+                          grid_dwf_cache_t** out);
+int grid_dwf_cache_destroy(grid_dwf_cache_t* c);
+int grid_dwf_cache_advise(grid_dwf_cache_t* c, void* host, size_t bytes, int advice);
+int grid_dwf_cache_open(grid_dwf_cache_t* c, void* host, size_t bytes, int intent, void** ptr);
+int grid_dwf_cache_close(grid_dwf_cache_t* c, void* host);
+int grid_dwf_cache_flush(grid_dwf_cache_t* c);
+int grid_dwf_cache_forget(grid_dwf_cache_t* c, void* host);
+int grid_dwf_cache_query(const grid_dwf_cache_t* c, const void* host, int* state, int* views, void** dev);
+int grid_dwf_cache_get_stats(const grid_dwf_cache_t* c, grid_dwf_cache_stats* st);
+const char* grid_dwf_cache_last_error(const grid_dwf_cache_t* c);
+
 /* |a|^2 (b == NULL) or a^+ b with FP64 accumulation, like grid_dwf_norm2 / grid_dwf_inner, for
  * callers that cannot allocate device memory: code recording a CUDA graph (where cudaMalloc is
  * not allowed), loops that must not take cudaMalloc's implicit device synchronisation, or a host

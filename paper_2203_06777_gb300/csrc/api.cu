@@ -46,6 +46,9 @@ struct grid_dwf {
   // walk of the packed hopping launches in z-blocks of this many planes (-1: automatic; the
   // environment variable GRID_DWF_ZBLOCK, read at create, overrides it; 0 = lexicographic)
   int zblk = -1;
+  // CG: the inner iteration whose residual decides a reliable update, counted back from the
+  // current one (-1: automatic; GRID_DWF_CG_LAG, read at create, overrides it)
+  int cg_lag = -1;
   int fp64_arith = GRID_DWF_FP64_ARITH_NATIVE;  // arithmetic of the FP64 hopping term
 };
 
@@ -363,6 +366,8 @@ int grid_dwf_create(const int dims[4], int Ls, double M5, double mass, const int
   h->sync_debug = sd && sd[0] == '1';
   const char* zbe = std::getenv("GRID_DWF_ZBLOCK");
   if (zbe) h->zblk = std::atoi(zbe);
+  const char* lge = std::getenv("GRID_DWF_CG_LAG");
+  if (lge) h->cg_lag = std::atoi(lge) > 0 ? 1 : 0;
   cudaGetDevice(&h->device);
   cudaError_t e = cudaMalloc(&h->partials, sizeof(double) * 2 * RED_BLOCKS);
   if (e == cudaSuccess) e = cudaMalloc(&h->scal, sizeof(double) * S_COUNT);
@@ -685,12 +690,8 @@ int cg_normal(grid_dwf_t* h, const void* rhs, void* xo_, double tol, int maxiter
     // The normal operator's launches with the vector algebra fused (18-real links): p^+ A p is
     // |Mpc p|^2, summed in the epilogue of Mpc's second launch, and r -= alpha A p happens in the
     // epilogue of Mpc^+'s second launch, so A p is never stored. Partial sums: one per CTA.
-    // Both use the FP32 results before they are rounded to the storage format. With BF16 storage
-    // (8 significant bits) that departs enough from the rounded fields the next iteration reads
-    // to cost iterations (24^4 x 12: 312 instead of 225), so BF16 keeps the separate passes,
-    // whose p^+ A p and update both use the stored A p; FP32 and FP16 take the same number of
-    // iterations either way (170 / 169 and 171 / 169).
-    const bool fused = !h->c12 && PS != GRID_DWF_BF16;
+    // Both use the FP32 results before they are rounded to the storage format.
+    const bool fused = !h->c12;
     double* red = nullptr;
     int nred = 0;
     if (fused) {
@@ -701,6 +702,11 @@ int cg_normal(grid_dwf_t* h, const void* rhs, void* xo_, double tol, int maxiter
       red = static_cast<double*>(rp);
     }
     int last_update = 0;  // iteration of the last reliable update (its |r|^2 is on another scale)
+    // The decision reads the previous iteration's residual (the GPU never waits for the host)
+    // except with BF16 storage, whose 8-bit recursion drifts fast enough that one iteration's
+    // delay before each reliable update cost it 309 iterations instead of 225 at 24^4 x 12 (FP32:
+    // 170 / 169 at the same time; FP16: 171 / 169, and 0.230 s against 0.244 s).
+    const int lag = h->cg_lag >= 0 ? h->cg_lag : (PS == GRID_DWF_BF16 ? 0 : 1);
     while (!converged && iters < maxiter) {
       if (fused) {
         CgEpilogue norm;
@@ -732,8 +738,8 @@ int cg_normal(grid_dwf_t* h, const void* rhs, void* xo_, double tol, int maxiter
          "cg residual copy");
       CK(cudaEventRecord(h->ring_ev[slot], h->stream), "cg residual copy");
       bool reliable = iters == maxiter;
-      if (iters - 1 > last_update) {
-        const int prev = (iters - 1) % grid_dwf::RING;
+      if (iters - lag > last_update) {
+        const int prev = (iters - lag) % grid_dwf::RING;
         CK(cudaEventSynchronize(h->ring_ev[prev]), "cg residual read");
         const double rp = h->host_ring[prev];
         if (!is_finite(rp)) return fail(h, GRID_DWF_ERR_NONFINITE, "cg: non-finite sloppy residual");

@@ -1045,13 +1045,14 @@ __device__ __forceinline__ void dhop_body_lane64(const DhopArgs& a) {
 }
 
 // Register budget. Every launch of dhop_kernel has at most 128 threads (128 / threads-per-site
-// whole sites). The packed kernels keep four such CTAs per SM (128 registers per thread), except
-// FP16 storage, measured fastest with three (168 registers: its mixed-precision projection keeps
-// more values live); the FP64 kernel is bound by the FP64 pipe and keeps more registers instead.
+// whole sites). The packed kernels keep four such CTAs per SM (128 registers per thread, no
+// spills; measured against three CTAs with 156-168 registers: FP16 storage 43.1 -> 41.0 us at
+// 16^4 x 16 and 633 -> 586 us at 32^4 x 16, FP32 and BF16 within 1-2%); the FP64 kernel is
+// bound by the FP64 pipe and keeps more registers instead.
 template <int P>
 struct DhopOccupancy {
   static constexpr int THREADS = 128;
-  static constexpr int MIN_BLOCKS = (P == P64) ? 1 : (P == P16) ? 3 : 4;
+  static constexpr int MIN_BLOCKS = (P == P64) ? 1 : 4;
 };
 
 // Threads per site: slice pairs (packed kernels) or padded slices (FP64).

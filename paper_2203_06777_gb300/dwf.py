@@ -57,6 +57,22 @@ class _CgStats(ctypes.Structure):
                 ("true_residual", ctypes.c_double), ("seconds", ctypes.c_double), ("flops", ctypes.c_double)]
 
 
+class _CacheStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_ulonglong) for n in ("hits", "misses", "evictions", "cpu_opens", "copies_to_device",
+                                                   "copies_to_host", "bytes_to_device", "bytes_to_host")] + \
+               [("peak_resident", ctypes.c_size_t), ("resident_bytes", ctypes.c_size_t)]
+
+
+class CacheBackend(ctypes.Structure):
+    """Data motion of a FieldCache (grid_dwf_cache_backend): device allocation, free and the two
+    copies as C callbacks returning 0 on success."""
+    _ALLOC = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p))
+    _FREE = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
+    _COPY = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t)
+    _fields_ = [("ctx", ctypes.c_void_p), ("alloc", _ALLOC), ("free", _FREE), ("to_device", _COPY),
+                ("to_host", _COPY)]
+
+
 @dataclass
 class CgStats:
     iterations: int
@@ -101,6 +117,15 @@ def load(build: bool = True):
             "grid_dwf_force": [vp, i, vp, vp, vp, vp, dp],
             "grid_dwf_pf_force": [vp, vp, vp, d, i, i, i, vp, vp, dp, ctypes.POINTER(_CgStats)],
             "grid_dwf_pipe_peak": [i, vp, dp],
+            "grid_dwf_cache_create": [ctypes.c_size_t, vp, vp, ctypes.POINTER(vp)],
+            "grid_dwf_cache_destroy": [vp],
+            "grid_dwf_cache_advise": [vp, vp, ctypes.c_size_t, i],
+            "grid_dwf_cache_open": [vp, vp, ctypes.c_size_t, i, ctypes.POINTER(vp)],
+            "grid_dwf_cache_close": [vp, vp],
+            "grid_dwf_cache_flush": [vp],
+            "grid_dwf_cache_forget": [vp, vp],
+            "grid_dwf_cache_query": [vp, vp, ip, ip, ctypes.POINTER(vp)],
+            "grid_dwf_cache_get_stats": [vp, ctypes.POINTER(_CacheStats)],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -110,6 +135,8 @@ def load(build: bool = True):
         lib.grid_dwf_last_error.restype = ctypes.c_char_p
         lib.grid_dwf_status_string.argtypes = [i]
         lib.grid_dwf_status_string.restype = ctypes.c_char_p
+        lib.grid_dwf_cache_last_error.argtypes = [vp]
+        lib.grid_dwf_cache_last_error.restype = ctypes.c_char_p
         _lib = lib
         return lib
 
@@ -420,3 +447,101 @@ class PseudofermionAction(torch.autograd.Function):
 
 def pseudofermion_action(phi, U, op: GridDWF, tol=1e-12, mode=CG_FP64):
     return PseudofermionAction.apply(phi, U, op, tol, mode)
+
+
+# ---------------------------------------------------------------- software-managed device cache
+
+CPU_READ, CPU_WRITE, ACC_READ, ACC_WRITE, ACC_WRITE_DISCARD = 0, 1, 2, 3, 4
+ADVISE_NORMAL, ADVISE_INFREQUENT = 0, 1
+CACHE_EMPTY, CACHE_CONSISTENT, CACHE_HOST_NEWER, CACHE_DEVICE_NEWER = 0, 1, 2, 3
+
+
+class _DeviceArray:
+    """A raw device buffer presented to torch through the CUDA array interface (no copy)."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None, "stream": None}
+
+
+_TYPESTR = {torch.float64: "<f8", torch.float32: "<f4", torch.float16: "<f2"}
+
+
+class FieldCache:
+    """Host fields paged through a bounded device footprint (grid_dwf_cache_*): views with an
+    access intent move whole fields between host and device; least recently used fields are
+    evicted, infrequently used (advised) ones first. Host fields are CPU tensors (pinned for
+    asynchronous copies). With a CacheBackend the data motion is the caller's (no GPU needed)."""
+
+    def __init__(self, high_watermark: int, backend: CacheBackend | None = None, stream=None):
+        self.lib = load()
+        self._backend = backend  # keeps the callbacks alive
+        h = ctypes.c_void_p()
+        if stream is None and backend is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        rc = self.lib.grid_dwf_cache_create(int(high_watermark), _ptr(stream) if stream else None,
+                                            ctypes.byref(backend) if backend is not None else None, ctypes.byref(h))
+        if rc != 0:
+            raise GridDWFError(rc, "grid_dwf_cache_create failed")
+        self._h = h
+
+    def close_cache(self):
+        if getattr(self, "_h", None):
+            self.lib.grid_dwf_cache_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close_cache()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc != 0:
+            raise GridDWFError(rc, f"{what}: {self.lib.grid_dwf_cache_last_error(self._h).decode()}")
+
+    @staticmethod
+    def _host(t):
+        if isinstance(t, torch.Tensor):
+            assert t.device.type == "cpu" and t.is_contiguous()
+            return t.data_ptr(), t.numel() * t.element_size()
+        return t.ctypes.data, t.nbytes  # numpy
+
+    def advise(self, host, advice):
+        p, n = self._host(host)
+        self._check(self.lib.grid_dwf_cache_advise(self._h, _ptr(p), n, advice), "advise")
+
+    def open(self, host, intent) -> int:
+        """Open a view; returns the device pointer (accelerator intents) or the host pointer."""
+        p, n = self._host(host)
+        out = ctypes.c_void_p()
+        self._check(self.lib.grid_dwf_cache_open(self._h, _ptr(p), n, intent, ctypes.byref(out)), "open")
+        return out.value
+
+    def device_view(self, host: torch.Tensor, intent) -> torch.Tensor:
+        """Open an accelerator view and wrap it as a CUDA tensor of the host tensor's shape."""
+        ptr = self.open(host, intent)
+        return torch.as_tensor(_DeviceArray(ptr, host.shape, _TYPESTR[host.dtype]), device="cuda")
+
+    def close(self, host):
+        p, _ = self._host(host)
+        self._check(self.lib.grid_dwf_cache_close(self._h, _ptr(p)), "close")
+
+    def flush(self):
+        self._check(self.lib.grid_dwf_cache_flush(self._h), "flush")
+
+    def forget(self, host):
+        p, _ = self._host(host)
+        self._check(self.lib.grid_dwf_cache_forget(self._h, _ptr(p)), "forget")
+
+    def query(self, host):
+        p, _ = self._host(host)
+        st, views, dev = ctypes.c_int(), ctypes.c_int(), ctypes.c_void_p()
+        self._check(self.lib.grid_dwf_cache_query(self._h, _ptr(p), ctypes.byref(st), ctypes.byref(views),
+                                                  ctypes.byref(dev)), "query")
+        return st.value, views.value, dev.value
+
+    def stats(self) -> dict:
+        st = _CacheStats()
+        self._check(self.lib.grid_dwf_cache_get_stats(self._h, ctypes.byref(st)), "stats")
+        return {n: getattr(st, n) for n, _ in _CacheStats._fields_}
