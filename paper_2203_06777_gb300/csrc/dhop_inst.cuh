@@ -29,7 +29,24 @@ static cudaError_t launch_one(const DhopArgs& a, int threads, int blocks, size_t
     m.blocks1 = full;
     m.red_base = 0;
     m.own_from = 0;
-    if (full > 0) kern<<<halves * full, threads, smem, stream>>>(m);
+    if (full > 0) {
+      if (a.pdl) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(halves * full);
+        cfg.blockDim = dim3(threads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaError_t e = cudaLaunchKernelEx(&cfg, kern, m);
+        if (e != cudaSuccess) return e;
+      } else {
+        kern<<<halves * full, threads, smem, stream>>>(m);
+      }
+    }
     if (full * a.sites_per_cta != a.g.N4h) {
       DhopArgs t = a;
       t.site_base = a.g.N4h - a.sites_per_cta;

@@ -57,6 +57,7 @@ struct DhopArgs {
   // CG epilogues of the packed kernels (EPI_NORM, EPI_AXPY; one half per launch): FP64 partial
   // sums, one per CTA, go to red[red_base + CTA index]; a thread adds nothing (and, for EPI_AXPY,
   // stores nothing) for a site below own_from, which a previous launch already covered.
+  int pdl;  // host side: launch the packed kernel as a programmatic dependent of the previous one
   double* red;
   int red_base;
   int own_from;
@@ -763,6 +764,12 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
     cb_coords(a.g, site, out_parity, c);
 #pragma unroll
     for (int h = 0; h < 8; ++h) nb[h] = cb_neighbour(a.g, site, c, h >> 1, (h & 1) == 0, phs[h]);
+    // Launched as a programmatic dependent of the previous kernel on the stream, the CTA may start
+    // before that kernel has finished: everything above reads only the launch arguments; wait for
+    // the previous grid (its writes visible) before the first load of memory it may have written,
+    // the links included (they are packed lazily by a kernel that can precede this one). Without
+    // a dependency this returns at once.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     for (int h = q; h < 8; h += Lsh) {
       const int mu = h >> 1;
       const char* src = (h & 1) == 0 ? Uo + ((size_t)site * 4 + mu) * LB : Ui + ((size_t)nb[h] * 4 + mu) * LB;
@@ -810,6 +817,10 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
       }
     }
   }
+
+  // The next kernel on the stream may be scheduled once every CTA has passed this point (it then
+  // waits at its own griddepcontrol.wait for this grid to finish); without one this does nothing.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
   // ------------------------------------------------------------ epilogue
   char* outb = static_cast<char*>(second ? a.out2 : a.out) + site_offset(site, Lsh, site_bytes);
