@@ -87,7 +87,16 @@ typedef struct {
  * (antiperiodic), NULL meaning {+1, +1, +1, -1}; compress12 != 0 stores links as two rows (the
  * third rebuilt as the conjugated cross product, exact for SU(3) links); stream is a
  * cudaStream_t (NULL = legacy default stream). Uses the current CUDA device. On success *out
- * owns device memory for the links and workspaces, freed by grid_dwf_destroy. */
+ * owns device memory for the links and workspaces, freed by grid_dwf_destroy.
+ * Tuning read from the environment at create (results are the same bit for bit; only the speed
+ * changes): GRID_DWF_ZBLOCK (CTA walk of the FP32/FP16/BF16 hops in blocks of that many z-planes;
+ * default: 8 for FP32 fields larger than ~96 MB, else the lexicographic walk, 0), GRID_DWF_PDL
+ * (0 disables launching those hops as programmatic dependents of the previous kernel; default 1),
+ * GRID_DWF_SITES_PER_CTA (fewer sites per CTA than fill 128 threads), GRID_DWF_SYNC_DEBUG (1:
+ * synchronise after every call to surface asynchronous errors at their call). GRID_DWF_CG_LAG (0 or
+ * 1) chooses whether the mixed CG decides its reliable updates on the current or the previous
+ * inner residual (default 1, and 0 for BF16), which changes the iterates, not the convergence
+ * criterion. */
 int grid_dwf_create(const int dims[4], int Ls, double M5, double mass, const int bc[4], int compress12, void* stream,
                     grid_dwf_t** out);
 int grid_dwf_destroy(grid_dwf_t* h);
@@ -250,7 +259,9 @@ int grid_dwf_pipe_peak(int kind, void* stream, double* gflops);
  *   flush    writes every newer, unpinned device copy back to the host (the copies stay).
  *   forget   writes back and drops one field's entry and device buffer.
  *   query    the entry's state (0 empty: no device copy, 1 consistent, 2 host newer, 3 device
- *            newer), its open accelerator views and device pointer (for tests and tools). */
+ *            newer), its open accelerator views and device pointer (for tests and tools).
+ * A cache is not safe for concurrent calls from several host threads; use one per thread or
+ * serialise the calls. */
 typedef struct grid_dwf_cache grid_dwf_cache_t;
 enum { GRID_DWF_CPU_READ = 0, GRID_DWF_CPU_WRITE = 1, GRID_DWF_ACC_READ = 2, GRID_DWF_ACC_WRITE = 3,
        GRID_DWF_ACC_WRITE_DISCARD = 4 };

@@ -54,6 +54,9 @@ struct grid_dwf {
   // their first load) for it to finish; 16^4 x 16 FP32 59.0 -> 56.3 us, FP16 41.1 -> 39.1 us per
   // full-lattice launch, bit-identical results (GRID_DWF_PDL=0, read at create, turns it off)
   int pdl = 1;
+  // sites per CTA of the packed hopping kernels if smaller than the 128-thread default (0: the
+  // default; GRID_DWF_SITES_PER_CTA, read at create, sets it)
+  int spc = 0;
   int fp64_arith = GRID_DWF_FP64_ARITH_NATIVE;  // arithmetic of the FP64 hopping term
 };
 
@@ -184,6 +187,16 @@ int ensure_gauge(grid_dwf_t* h, int prec) {
   return GRID_DWF_OK;
 }
 
+// Whole sites per CTA of a hopping launch: as many as fill 128 threads (one per slice pair, or per
+// slice in FP64), at most the half lattice; the packed kernels take fewer if the handle says so.
+int hop_sites_per_cta(const grid_dwf_t* h, int prec) {
+  int spc = 128 / dhop_threads_per_site(prec, h->Ls);
+  if (prec != GRID_DWF_FP64 && h->spc > 0 && h->spc < spc) spc = h->spc;
+  if (spc < 1) spc = 1;
+  if (spc > h->g.N4h) spc = h->g.N4h;  // tiny lattices: one full CTA
+  return spc;
+}
+
 // One half-lattice hopping application with its fused epilogue.
 int dhop_half(grid_dwf_t* h, int prec, const void* in, void* out, int out_parity, bool dag, int pre, int post,
               double alpha, double beta, const void* aux, const void* in2 = nullptr, void* out2 = nullptr,
@@ -208,9 +221,7 @@ int dhop_half(grid_dwf_t* h, int prec, const void* in, void* out, int out_parity
   a.g = h->g;
   a.out_parity = out_parity;
   a.nsg = dhop_threads_per_site(prec, h->Ls);
-  a.sites_per_cta = 128 / a.nsg;
-  if (a.sites_per_cta < 1) a.sites_per_cta = 1;
-  if (a.sites_per_cta > h->g.N4h) a.sites_per_cta = h->g.N4h;  // tiny lattices: one full CTA
+  a.sites_per_cta = hop_sites_per_cta(h, prec);
   a.pre = pre;
   a.post = post;
   a.site_base = 0;
@@ -372,6 +383,8 @@ int grid_dwf_create(const int dims[4], int Ls, double M5, double mass, const int
   h->sync_debug = sd && sd[0] == '1';
   const char* zbe = std::getenv("GRID_DWF_ZBLOCK");
   if (zbe) h->zblk = std::atoi(zbe);
+  const char* spce = std::getenv("GRID_DWF_SITES_PER_CTA");
+  if (spce) h->spc = std::atoi(spce);
   const char* pdle = std::getenv("GRID_DWF_PDL");
   if (pdle) h->pdl = std::atoi(pdle) != 0;
   const char* lge = std::getenv("GRID_DWF_CG_LAG");
@@ -703,7 +716,7 @@ int cg_normal(grid_dwf_t* h, const void* rhs, void* xo_, double tol, int maxiter
     double* red = nullptr;
     int nred = 0;
     if (fused) {
-      const int spc = std::max(1, std::min(128 / dhop_threads_per_site(PS, Ls), (int)N));
+      const int spc = hop_sites_per_cta(h, PS);
       nred = (int)(N / spc) + (N % spc ? 1 : 0);  // the full CTAs, and the end CTA if there is one
       void* rp = nullptr;
       RET(ws_get(h, WS_CG_RED, sizeof(double) * (size_t)nred, &rp));
