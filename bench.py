@@ -234,7 +234,7 @@ def launches_per_step(op, prec, dwf) -> int:
     if prec == dwf.FP64:
         return 2
     lsh = (op.Ls + 1) // 2
-    spc = min(max(1, 128 // lsh), op.half_sites)
+    spc = min(max(1, 8 if lsh == 8 else 128 // lsh), op.half_sites)
     return 1 if op.half_sites % spc == 0 else 2
 
 

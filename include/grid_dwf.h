@@ -221,6 +221,32 @@ int grid_dwf_force(grid_dwf_t* h, int precision, const void* psi, void* chi, dou
 int grid_dwf_pf_force(grid_dwf_t* h, const void* phi, void* X, double tol, int maxiter, int mode, int precision,
                       double* F, double* G, double* S_out, grid_dwf_cg_stats* stats);
 
+/* A lattice split into blocks along t (one block per handle: dims[3] is the block's extent, even,
+ * its first t-plane at an even global t). Source: the paper's Section 3, whose multi-GPU runs
+ * assemble the faces of each GPU's block in their own kernels and overlap the exchange with the
+ * interior of the hopping term. Per hop of output parity p, each block
+ *   - projects its input half field (parity 1 - p) on its first t-plane with the forward-hop
+ *     projector and on its last t-plane with the backward-hop projector (grid_dwf_face_project;
+ *     phase_first / phase_last: the boundary phase bc[t] if that face crosses the global lattice
+ *     edge, else +1; dag as for the hop), and sends send_first to the previous block and
+ *     send_last to the next one (the caller moves them, e.g. by peer copies into local buffers);
+ *   - computes its interior (all output sites off the two face planes: their neighbours are local)
+ *     with grid_dwf_dhop_region(..., GRID_DWF_REGION_INTERIOR, NULL, NULL, NULL) while the faces
+ *     travel, then its two face planes with GRID_DWF_REGION_FACES, recv_fwd = the next block's
+ *     send_first, recv_bwd = the previous block's send_last, links_bwd = the previous block's
+ *     grid_dwf_face_links(prec, p) (the links U_t of its last plane, exchanged once per gauge field).
+ * Faces are FP32 half spinors, [face site][6][slice pair] 16-byte vectors, face site = cb index
+ * within the t-plane (grid_dwf_face_bytes gives the size, link faces are in the stored link
+ * format); the result equals the hop of the whole lattice bit for bit. FP32, FP16 and BF16 fields;
+ * each t-plane must hold whole CTAs of sites (GRID_DWF_ERR_INVALID_ARG otherwise). */
+enum { GRID_DWF_REGION_INTERIOR = 0, GRID_DWF_REGION_FACES = 1 };
+int grid_dwf_face_bytes(const grid_dwf_t* h, int precision, size_t* face_bytes, size_t* link_face_bytes);
+int grid_dwf_face_project(grid_dwf_t* h, int precision, const void* in, int dag, int phase_first, int phase_last,
+                          void* send_first, void* send_last);
+int grid_dwf_face_links(grid_dwf_t* h, int precision, int out_parity, void* links_last);
+int grid_dwf_dhop_region(grid_dwf_t* h, int precision, const void* in, void* out, int out_parity, int dag,
+                         int region, const void* recv_fwd, const void* recv_bwd, const void* links_bwd);
+
 /* Measured arithmetic ceiling of the current device, the denominator of the roofline of a kernel
  * bound by its arithmetic pipe rather than by memory (the IEEE FP64 hopping term on this GPU):
  * FP64 FMA, scalar FP32 FMA or packed FP32x2 FMA throughput, in GFLOP/s (2 flops per FMA, 4 per

@@ -16,6 +16,8 @@
 #include "site_ops.cuh"
 
 namespace gdwf {
+cudaError_t launch_face_project(int prec, bool dag, const Geom& g, int plane, const void* in, float ph_first,
+                                float ph_last, void* send_first, void* send_last, cudaStream_t st);
 cudaError_t launch_force(int prec, bool c12, const Geom& g, const void* psi, const void* chi, const void* Ue,
                          const void* Uo, double* F, double* G, double coef, bool float_float, cudaStream_t st);
 }
@@ -105,6 +107,16 @@ struct CgEpilogue {
   const double* coef = nullptr;
 };
 
+// Optional site range of a packed half-lattice hop (sites site_base .. site_base + nsites - 1) and,
+// for the face planes of a block of a lattice split in t, the received faces and links.
+struct HopRegion {
+  int site_base = 0;
+  int nsites = 0;
+  const void* halo_fwd = nullptr;
+  const void* halo_bwd = nullptr;
+  const void* halo_links = nullptr;
+};
+
 int fail(grid_dwf_t* h, int code, const std::string& msg) {
   if (h) h->err = msg;
   return code;
@@ -188,9 +200,13 @@ int ensure_gauge(grid_dwf_t* h, int prec) {
 }
 
 // Whole sites per CTA of a hopping launch: as many as fill 128 threads (one per slice pair, or per
-// slice in FP64), at most the half lattice; the packed kernels take fewer if the handle says so.
+// slice in FP64), at most the half lattice; the packed kernels take fewer if the handle says so,
+// and 8 (64 threads) for 8 slice pairs: measured at Ls = 16, 16 -> 8 sites per CTA (same warps
+// per SM, a finer last wave) took the FP32 hop from 56.4 to 55.9 us at 16^4 and from 842 to
+// 822 us at 32^4, FP16 from 589 to 580 us at 32^4, bit-identical.
 int hop_sites_per_cta(const grid_dwf_t* h, int prec) {
   int spc = 128 / dhop_threads_per_site(prec, h->Ls);
+  if (prec != GRID_DWF_FP64 && ls_half(h->Ls) == 8) spc = 8;
   if (prec != GRID_DWF_FP64 && h->spc > 0 && h->spc < spc) spc = h->spc;
   if (spc < 1) spc = 1;
   if (spc > h->g.N4h) spc = h->g.N4h;  // tiny lattices: one full CTA
@@ -200,9 +216,15 @@ int hop_sites_per_cta(const grid_dwf_t* h, int prec) {
 // One half-lattice hopping application with its fused epilogue.
 int dhop_half(grid_dwf_t* h, int prec, const void* in, void* out, int out_parity, bool dag, int pre, int post,
               double alpha, double beta, const void* aux, const void* in2 = nullptr, void* out2 = nullptr,
-              const void* aux2 = nullptr, const CgEpilogue& epi = CgEpilogue()) {
+              const void* aux2 = nullptr, const CgEpilogue& epi = CgEpilogue(),
+              const HopRegion& region = HopRegion()) {
   RET(ensure_gauge(h, prec));
   DhopArgs a;
+  a.halo_fwd = region.halo_fwd;
+  a.halo_bwd = region.halo_bwd;
+  a.halo_links = region.halo_links;
+  a.plane = h->g.Lxh * h->g.L[1] * h->g.L[2];
+  a.region_sites = region.nsites;
   a.red = epi.red;
   a.r = epi.r;
   a.axpy_coef = epi.coef;
@@ -224,7 +246,7 @@ int dhop_half(grid_dwf_t* h, int prec, const void* in, void* out, int out_parity
   a.sites_per_cta = hop_sites_per_cta(h, prec);
   a.pre = pre;
   a.post = post;
-  a.site_base = 0;
+  a.site_base = region.site_base;
   a.zblk = 0;
   a.ctas_per_plane = 1;
   {
@@ -235,7 +257,8 @@ int dhop_half(grid_dwf_t* h, int prec, const void* in, void* out, int out_parity
     const int plane = h->g.Lxh * h->g.L[1];
     int zb = h->zblk;
     if (zb < 0) zb = (prec == GRID_DWF_FP32 && half_bytes(h, prec) > ((size_t)96 << 20)) ? 8 : 0;
-    if (prec != GRID_DWF_FP64 && zb > 0 && zb < h->g.L[2] && h->g.L[2] % zb == 0 && plane % a.sites_per_cta == 0) {
+    if (prec != GRID_DWF_FP64 && region.nsites == 0 && zb > 0 && zb < h->g.L[2] && h->g.L[2] % zb == 0 &&
+        plane % a.sites_per_cta == 0) {
       a.zblk = zb;
       a.ctas_per_plane = plane / a.sites_per_cta;
       a.div_cpp = make_fastdiv((uint32_t)a.ctas_per_plane);
@@ -607,6 +630,104 @@ int grid_dwf_inner(grid_dwf_t* h, int precision, int subset, const void* a, cons
   result[0] = h->host_scal[S_TMP0];
   result[1] = h->host_scal[S_TMP1];
   return GRID_DWF_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+// ---------------------------------------------------------------- blocks of a lattice split in t
+
+namespace {
+int halo_checks(grid_dwf_t* h, int precision) {
+  if (precision != GRID_DWF_FP32 && precision != GRID_DWF_FP16 && precision != GRID_DWF_BF16)
+    return fail(h, GRID_DWF_ERR_INVALID_ARG, "halo: FP32, FP16 or BF16 fields only");
+  const int plane = h->g.Lxh * h->g.L[1] * h->g.L[2];
+  if (plane % hop_sites_per_cta(h, precision) != 0)
+    return fail(h, GRID_DWF_ERR_INVALID_ARG, "halo: a t-plane must hold whole CTAs of sites");
+  return GRID_DWF_OK;
+}
+}  // namespace
+
+int grid_dwf_face_bytes(const grid_dwf_t* h, int precision, size_t* face_bytes, size_t* link_face_bytes) {
+  if (!h || !face_bytes || !link_face_bytes || !valid_prec(precision)) return GRID_DWF_ERR_INVALID_ARG;
+  const size_t plane = (size_t)h->g.Lxh * h->g.L[1] * h->g.L[2];
+  *face_bytes = plane * ls_half(h->Ls) * 6 * 16;
+  *link_face_bytes = plane * link_bytes(prec_bytes(precision), h->c12);
+  return GRID_DWF_OK;
+}
+
+int grid_dwf_face_project(grid_dwf_t* h, int precision, const void* in, int dag, int phase_first, int phase_last,
+                          void* send_first, void* send_last) {
+  const NvtxRange nvtx_("grid_dwf_face_project");
+  if (!h) return GRID_DWF_ERR_INVALID_ARG;
+  RET(halo_checks(h, precision));
+  if ((phase_first != 1 && phase_first != -1) || (phase_last != 1 && phase_last != -1))
+    return fail(h, GRID_DWF_ERR_INVALID_ARG, "face_project: phases must be +1 or -1");
+  RET(check_ptr(h, in, "in"));
+  RET(check_ptr(h, send_first, "send_first"));
+  RET(check_ptr(h, send_last, "send_last"));
+  const int plane = h->g.Lxh * h->g.L[1] * h->g.L[2];
+  CK(launch_face_project(precision, dag != 0, h->g, plane, in, (float)phase_first, (float)phase_last, send_first,
+                         send_last, h->stream),
+     "face_project");
+  return finish(h, "face_project");
+}
+
+int grid_dwf_face_links(grid_dwf_t* h, int precision, int out_parity, void* links_last) {
+  const NvtxRange nvtx_("grid_dwf_face_links");
+  if (!h) return GRID_DWF_ERR_INVALID_ARG;
+  RET(halo_checks(h, precision));
+  if (out_parity != GRID_DWF_EVEN && out_parity != GRID_DWF_ODD)
+    return fail(h, GRID_DWF_ERR_INVALID_ARG, "face_links: parity must be EVEN or ODD");
+  RET(check_ptr(h, links_last, "links_last"));
+  RET(ensure_gauge(h, precision));
+  const size_t lb = link_bytes(prec_bytes(precision), h->c12);
+  const int plane = h->g.Lxh * h->g.L[1] * h->g.L[2];
+  const char* src = static_cast<const char*>(h->gauge[precision][1 - out_parity]) +
+                    ((size_t)(h->g.N4h - plane) * 4 + 3) * lb;
+  CK(cudaMemcpy2DAsync(links_last, lb, src, 4 * lb, lb, plane, cudaMemcpyDeviceToDevice, h->stream), "face_links");
+  return finish(h, "face_links");
+}
+
+int grid_dwf_dhop_region(grid_dwf_t* h, int precision, const void* in, void* out, int out_parity, int dag,
+                         int region, const void* recv_fwd, const void* recv_bwd, const void* links_bwd) {
+  const NvtxRange nvtx_("grid_dwf_dhop_region");
+  if (!h) return GRID_DWF_ERR_INVALID_ARG;
+  RET(halo_checks(h, precision));
+  if (out_parity != GRID_DWF_EVEN && out_parity != GRID_DWF_ODD)
+    return fail(h, GRID_DWF_ERR_INVALID_ARG, "dhop_region: parity must be EVEN or ODD");
+  if (region != GRID_DWF_REGION_INTERIOR && region != GRID_DWF_REGION_FACES)
+    return fail(h, GRID_DWF_ERR_INVALID_ARG, "dhop_region: region must be INTERIOR or FACES");
+  RET(check_ptr(h, in, "in"));
+  RET(check_ptr(h, out, "out"));
+  const size_t nb = half_bytes(h, precision);
+  if (overlap(in, nb, out, nb)) return fail(h, GRID_DWF_ERR_ALIAS, "dhop_region: out overlaps in");
+  const int plane = h->g.Lxh * h->g.L[1] * h->g.L[2];
+  if (region == GRID_DWF_REGION_INTERIOR) {
+    if (h->g.N4h > 2 * plane) {  // Lt >= 3
+      HopRegion r;
+      r.site_base = plane;
+      r.nsites = h->g.N4h - 2 * plane;
+      RET(dhop_half(h, precision, in, out, out_parity, dag != 0, PRE_NONE, POST_NONE, 1.0, 0.0, nullptr, nullptr,
+                    nullptr, nullptr, CgEpilogue(), r));
+    }
+    return finish(h, "dhop_region");
+  }
+  RET(check_ptr(h, recv_fwd, "recv_fwd"));
+  RET(check_ptr(h, recv_bwd, "recv_bwd"));
+  RET(check_ptr(h, links_bwd, "links_bwd"));
+  for (int k = 0; k < 2; ++k) {  // the first t-plane, then the last
+    HopRegion r;
+    r.site_base = k == 0 ? 0 : h->g.N4h - plane;
+    r.nsites = plane;
+    r.halo_fwd = recv_fwd;
+    r.halo_bwd = recv_bwd;
+    r.halo_links = links_bwd;
+    RET(dhop_half(h, precision, in, out, out_parity, dag != 0, PRE_NONE, POST_NONE, 1.0, 0.0, nullptr, nullptr,
+                  nullptr, nullptr, CgEpilogue(), r));
+  }
+  return finish(h, "dhop_region");
 }
 
 }  // extern "C"

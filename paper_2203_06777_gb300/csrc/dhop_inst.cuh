@@ -23,7 +23,8 @@ static cudaError_t launch_one(const DhopArgs& a, int threads, int blocks, size_t
     // in time. a.in2 != nullptr: both halves of a full-lattice hop in the same launches.
     // CG epilogues: partial sums [0, full) from the full CTAs, [full] from the end CTA, which adds
     // only the sites the full CTAs did not cover.
-    const int full = a.g.N4h / a.sites_per_cta;
+    const int nsites = a.region_sites > 0 ? a.region_sites : a.g.N4h;
+    const int full = nsites / a.sites_per_cta;
     const int halves = a.in2 ? 2 : 1;
     DhopArgs m = a;
     m.blocks1 = full;
@@ -47,7 +48,7 @@ static cudaError_t launch_one(const DhopArgs& a, int threads, int blocks, size_t
         kern<<<halves * full, threads, smem, stream>>>(m);
       }
     }
-    if (full * a.sites_per_cta != a.g.N4h) {
+    if (a.region_sites == 0 && full * a.sites_per_cta != a.g.N4h) {
       DhopArgs t = a;
       t.site_base = a.g.N4h - a.sites_per_cta;
       t.blocks1 = 1;
@@ -71,6 +72,13 @@ static cudaError_t launch_ls(const DhopArgs& a, bool dag, bool c12, int threads,
     // the instantiation with exactly the epilogue parts this launch uses; the CG epilogues exist
     // for the launches that use them only: Mpc's second launch (pre-operation Mooee, no dag) with
     // the norm, Mpc^+'s second launch (Mooee^+, dag) with the update, 18-real links
+    if (a.halo_fwd) {  // a face region of a block of a lattice split in t (plain hop)
+      if (a.pre != PRE_NONE || a.post != POST_NONE || a.red || a.in2) return cudaErrorInvalidValue;
+      if (dag) return c12 ? launch_one<true, true, LSC, EPI_HALO>(a, threads, blocks, smem, stream)
+                          : launch_one<true, false, LSC, EPI_HALO>(a, threads, blocks, smem, stream);
+      return c12 ? launch_one<false, true, LSC, EPI_HALO>(a, threads, blocks, smem, stream)
+                 : launch_one<false, false, LSC, EPI_HALO>(a, threads, blocks, smem, stream);
+    }
     if (a.red && !c12 && a.pre != PRE_NONE && a.post == POST_NONE) {
       if (a.r && dag) return launch_one<true, false, LSC, EPI_PRE | EPI_AXPY>(a, threads, blocks, smem, stream);
       if (!a.r && !dag) return launch_one<false, false, LSC, EPI_PRE | EPI_NORM>(a, threads, blocks, smem, stream);

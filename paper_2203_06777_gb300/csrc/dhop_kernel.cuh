@@ -58,6 +58,18 @@ struct DhopArgs {
   // sums, one per CTA, go to red[red_base + CTA index]; a thread adds nothing (and, for EPI_AXPY,
   // stores nothing) for a site below own_from, which a previous launch already covered.
   int pdl;  // host side: launch the packed kernel as a programmatic dependent of the previous one
+  // EPI_HALO (the lattice of this handle is one block of a lattice split in t): the t hops that
+  // leave the block read projected half spinors from halo_fwd (beyond the last plane) and
+  // halo_bwd (before the first plane), [face site][6][pair] float4 of FP32 values, face site =
+  // cb index within the plane; the backward link of the first plane comes from halo_links
+  // ([face site], stored link format). plane = checkerboard sites per t-plane.
+  const void* halo_fwd;
+  const void* halo_bwd;
+  const void* halo_links;
+  int plane;
+  // > 0: the launch covers only region_sites sites from site_base on (a multiple of
+  // sites_per_cta; one half), e.g. the interior or one face plane of a block
+  int region_sites;
   double* red;
   int red_base;
   int own_from;
@@ -691,7 +703,10 @@ __device__ __forceinline__ void mooee_inv_line(R* v, int Ls, bool forward_form, 
 //   EPI_AXPY (8): do not store the result; update the FP32 field r -= c * result with c read from
 //                 device memory (the CG step length), and add |r|^2 to the partial sums.
 // Neither is combined with a post-operation or with a full-lattice launch.
-enum EpiKind : int { EPI_NONE = 0, EPI_PRE = 1, EPI_POST = 2, EPI_BOTH = 3, EPI_NORM = 4, EPI_AXPY = 8 };
+//   EPI_HALO (16): the lattice is one block of a lattice split in t (see DhopArgs): hops that leave
+//                 the block in t take the neighbours' projected faces; launched over the face
+//                 planes only (the interior needs no halo and runs the plain instantiation).
+enum EpiKind : int { EPI_NONE = 0, EPI_PRE = 1, EPI_POST = 2, EPI_BOTH = 3, EPI_NORM = 4, EPI_AXPY = 8, EPI_HALO = 16 };
 
 // Sum of one value per thread over the CTA in a fixed order (warp shuffles, then the warps in
 // order), written by thread 0 to *dst.
@@ -759,11 +774,16 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
   // Neighbour indices and boundary phases of the eight hops, all computed before the first load
   // so that the hop loop below is straight-line code whose loads the compiler can issue early.
   int nb[8], phs[8];
+  bool edge_lo = false, edge_hi = false;  // EPI_HALO: first / last t-plane of the block
   {
     int c[4];
     cb_coords(a.g, site, out_parity, c);
 #pragma unroll
     for (int h = 0; h < 8; ++h) nb[h] = cb_neighbour(a.g, site, c, h >> 1, (h & 1) == 0, phs[h]);
+    if constexpr ((EK & EPI_HALO) != 0) {
+      edge_lo = c[3] == 0;
+      edge_hi = c[3] == a.g.L[3] - 1;
+    }
     // Launched as a programmatic dependent of the previous kernel on the stream, the CTA may start
     // before that kernel has finished: everything above reads only the launch arguments; wait for
     // the previous grid (its writes visible) before the first load of memory it may have written,
@@ -773,6 +793,8 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
     for (int h = q; h < 8; h += Lsh) {
       const int mu = h >> 1;
       const char* src = (h & 1) == 0 ? Uo + ((size_t)site * 4 + mu) * LB : Ui + ((size_t)nb[h] * 4 + mu) * LB;
+      if ((EK & EPI_HALO) != 0 && h == 7 && edge_lo)  // U_t(x - t) lives on the previous block
+        src = static_cast<const char*>(a.halo_links) + (size_t)site * LB;
       stage_link_f32<P, C12>(lsm + h * DHOP_LINK_F32_BYTES, src);
     }
   }
@@ -790,7 +812,20 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
       float2 h[12], uh[12];
       float u[18];
       const char* nbp = in + site_offset(nb[hop], Lsh, site_bytes);
-      if constexpr (P == P32) {
+      bool from_halo = false;
+      if constexpr ((EK & EPI_HALO) != 0) from_halo = (hop == 6 && edge_hi) || (hop == 7 && edge_lo);
+      if (from_halo) {
+        // the neighbour block's projected half spinor, already multiplied by any boundary phase
+        const int f = hop == 6 ? site - (a.g.N4h - a.plane) : site;
+        const float4* hp = static_cast<const float4*>(hop == 6 ? a.halo_fwd : a.halo_bwd) + (size_t)f * 6 * Lsh + q;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+          const float4 t = __ldg(hp + (size_t)j * Lsh);
+          h[2 * j] = make_float2(t.x, t.y);
+          h[2 * j + 1] = make_float2(t.z, t.w);
+        }
+        load_link_f32(lsm + hop * DHOP_LINK_F32_BYTES, u);
+      } else if constexpr (P == P32) {
         float2 psi[24];
         load_pair<P, LSHC>(nbp, q, Lsh, psi);
         load_link_f32(lsm + hop * DHOP_LINK_F32_BYTES, u);
@@ -807,7 +842,7 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
         else
           project2w<P, SB>(mu, w, h);
       }
-      const float cph = phs[hop] < 0 ? -alpha : alpha;
+      const float cph = (!from_halo && phs[hop] < 0) ? -alpha : alpha;
       if (fwd) {
         su3_mul2<false>(u, h, uh);
         accumulate2<SF>(mu, uh, cph, acc);

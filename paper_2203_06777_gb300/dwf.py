@@ -117,6 +117,10 @@ def load(build: bool = True):
             "grid_dwf_force": [vp, i, vp, vp, vp, vp, dp],
             "grid_dwf_pf_force": [vp, vp, vp, d, i, i, i, vp, vp, dp, ctypes.POINTER(_CgStats)],
             "grid_dwf_pipe_peak": [i, vp, dp],
+            "grid_dwf_face_bytes": [vp, i, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)],
+            "grid_dwf_face_project": [vp, i, vp, i, i, i, vp, vp],
+            "grid_dwf_face_links": [vp, i, i, vp],
+            "grid_dwf_dhop_region": [vp, i, vp, vp, i, i, i, vp, vp, vp],
             "grid_dwf_cache_create": [ctypes.c_size_t, vp, vp, ctypes.POINTER(vp)],
             "grid_dwf_cache_destroy": [vp],
             "grid_dwf_cache_advise": [vp, vp, ctypes.c_size_t, i],
@@ -301,6 +305,43 @@ class GridDWF:
         self._call("grid_dwf_dhop", prec, _ptr(f), _ptr(out), int(parity), int(dag))
         return out
 
+    # ---- a block of a lattice split in t (see grid_dwf_face_project / grid_dwf_dhop_region)
+
+    def face_buffers(self, prec):
+        """Empty (face, link face) device buffers of this block's sizes, as uint8 tensors."""
+        fb, lb = ctypes.c_size_t(), ctypes.c_size_t()
+        rc = self.lib.grid_dwf_face_bytes(self._h, prec, ctypes.byref(fb), ctypes.byref(lb))
+        if rc != 0:
+            raise GridDWFError(rc, "grid_dwf_face_bytes")
+        return (torch.empty(fb.value, dtype=torch.uint8, device=self.device),
+                torch.empty(lb.value, dtype=torch.uint8, device=self.device))
+
+    def face_project(self, f_half: torch.Tensor, dag=False, phase_first=1, phase_last=1):
+        """(send_first, send_last): this block's first and last t-planes of the input half field,
+        projected for the previous and the next block's hops."""
+        prec = self._check_field(f_half)
+        a, _ = self.face_buffers(prec)
+        b = torch.empty_like(a)
+        self._call("grid_dwf_face_project", prec, _ptr(f_half), int(dag), int(phase_first), int(phase_last), _ptr(a),
+                   _ptr(b))
+        return a, b
+
+    def face_links(self, prec, out_parity):
+        """The links U_t of this block's last t-plane read by the next block's hops of out_parity."""
+        _, links = self.face_buffers(prec)
+        self._call("grid_dwf_face_links", prec, int(out_parity), _ptr(links))
+        return links
+
+    def dhop_region(self, f_half: torch.Tensor, out_parity, region, dag=False, out=None, recv_fwd=None,
+                    recv_bwd=None, links_bwd=None) -> torch.Tensor:
+        """The hop on this block's interior (REGION_INTERIOR) or its two face planes (REGION_FACES,
+        with the neighbours' faces and link face)."""
+        prec = self._check_field(f_half)
+        out = torch.empty_like(f_half) if out is None else out
+        self._call("grid_dwf_dhop_region", prec, _ptr(f_half), _ptr(out), int(out_parity), int(dag), int(region),
+                   _ptr(recv_fwd), _ptr(recv_bwd), _ptr(links_bwd))
+        return out
+
     def mooee(self, f: torch.Tensor, dag=False, inverse=False, out=None) -> torch.Tensor:
         prec = self._check_field(f)
         subset = self._subset_of(f)
@@ -451,6 +492,7 @@ def pseudofermion_action(phi, U, op: GridDWF, tol=1e-12, mode=CG_FP64):
 
 # ---------------------------------------------------------------- software-managed device cache
 
+REGION_INTERIOR, REGION_FACES = 0, 1
 CPU_READ, CPU_WRITE, ACC_READ, ACC_WRITE, ACC_WRITE_DISCARD = 0, 1, 2, 3, 4
 ADVISE_NORMAL, ADVISE_INFREQUENT = 0, 1
 CACHE_EMPTY, CACHE_CONSISTENT, CACHE_HOST_NEWER, CACHE_DEVICE_NEWER = 0, 1, 2, 3
