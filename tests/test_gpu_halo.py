@@ -92,3 +92,33 @@ def test_region_calls_reject_bad_arguments(dwf):
         op.face_project(f, phase_first=2)
     assert e.value.code == -1
     op.close()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_interior_and_face_launches_write_only_their_sites(dwf, prec):
+    """The interior launch writes every site off the two face planes and no other; the face launch
+    writes the two planes and no other (sentinel bytes elsewhere survive)."""
+    dims, Ls = (8, 4, 4, 6), 16
+    op = dwf.GridDWF(dims, Ls, 1.8, 0.01, bc=BC)
+    op.set_gauge(torch.from_numpy(synth.random_gauge(dims, seed=621, eps=0.4)).cuda())
+    f = op.pack(torch.from_numpy(synth.random_spinor(dims, Ls, seed=622)).cuda(), prec, dwf.ODD)
+    a, b = op.face_project(f)
+    links = op.face_links(prec, dwf.EVEN)
+    site_reals = op.half_reals // op.half_sites
+    plane = dims[0] // 2 * dims[1] * dims[2]
+    nplanes = dims[3]
+    sentinel = torch.tensor(12345.0, dtype=f.dtype, device="cuda")
+    for region in (dwf.REGION_INTERIOR, dwf.REGION_FACES):
+        out = torch.full_like(f, float(sentinel))
+        op.dhop_region(f, dwf.EVEN, region, out=out, recv_fwd=a, recv_bwd=b, links_bwd=links)
+        torch.cuda.synchronize()
+        # sites are stored in blocks of 4; a t-plane holds whole blocks here (plane = 64 sites)
+        per_site = out.view(op.half_sites, site_reals)
+        face = torch.zeros(op.half_sites, dtype=torch.bool, device="cuda")
+        face[:plane] = True
+        face[(nplanes - 1) * plane:] = True
+        written = (per_site != sentinel).any(dim=1)
+        untouched = (per_site == sentinel).all(dim=1)
+        mine = face if region == dwf.REGION_FACES else ~face
+        assert bool(written[mine].all()) and bool(untouched[~mine].all()), region
+    op.close()
