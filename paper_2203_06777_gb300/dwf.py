@@ -513,7 +513,10 @@ class FieldCache:
     """Host fields paged through a bounded device footprint (grid_dwf_cache_*): views with an
     access intent move whole fields between host and device; least recently used fields are
     evicted, infrequently used (advised) ones first. Host fields are CPU tensors (pinned for
-    asynchronous copies). With a CacheBackend the data motion is the caller's (no GPU needed)."""
+    asynchronous copies) or NumPy arrays. The copies run on `stream` (default: torch's current
+    stream when the cache is created); kernels that use a view on another stream must be ordered
+    after the open on that stream. With a CacheBackend the data motion is the caller's (no GPU
+    needed)."""
 
     def __init__(self, high_watermark: int, backend: CacheBackend | None = None, stream=None):
         self.lib = load()
