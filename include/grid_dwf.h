@@ -96,7 +96,9 @@ typedef struct {
  * synchronise after every call to surface asynchronous errors at their call). GRID_DWF_CG_LAG (0 or
  * 1) chooses whether the mixed CG decides its reliable updates on the current or the previous
  * inner residual (default 1, and 0 for BF16), which changes the iterates, not the convergence
- * criterion. */
+ * criterion. GRID_DWF_CG_DELTA (a number in (0, 1)) sets the mixed CG's reliable-update threshold,
+ * the factor by which the inner residual must fall before x is folded into the FP64 solution and
+ * the FP64 residual recomputed (default 1e-4 for FP32 inner solves, 0.03 for FP16 and BF16). */
 int grid_dwf_create(const int dims[4], int Ls, double M5, double mass, const int bc[4], int compress12, void* stream,
                     grid_dwf_t** out);
 int grid_dwf_destroy(grid_dwf_t* h);

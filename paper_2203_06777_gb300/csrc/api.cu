@@ -32,6 +32,7 @@ struct grid_dwf {
   double d5 = 0, inv_d5 = 0, inv_den = 0;
   cudaStream_t stream = nullptr;
   int device = 0;
+  size_t l2_bytes = (size_t)126 << 20;  // the device's L2 (read at create)
   double* U_canon = nullptr;            // canonical FP64 links, device
   void* gauge[4][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
   std::map<int, std::pair<void*, size_t>> ws;  // workspace buffers by id
@@ -51,6 +52,9 @@ struct grid_dwf {
   // CG: the inner iteration whose residual decides a reliable update, counted back from the
   // current one (-1: automatic; GRID_DWF_CG_LAG, read at create, overrides it)
   int cg_lag = -1;
+  // CG: the reliable-update threshold (the sloppy residual's drop since the last update); 0:
+  // automatic (GRID_DWF_CG_DELTA, read at create, overrides it)
+  double cg_delta = 0;
   // launch the packed hopping kernels as programmatic dependents of the previous kernel: the next
   // launch's CTAs become resident while the previous kernel's last CTAs run, and wait (before
   // their first load) for it to finish; 16^4 x 16 FP32 59.0 -> 56.3 us, FP16 41.1 -> 39.1 us per
@@ -200,13 +204,28 @@ int ensure_gauge(grid_dwf_t* h, int prec) {
 }
 
 // Whole sites per CTA of a hopping launch: as many as fill 128 threads (one per slice pair, or per
-// slice in FP64), at most the half lattice; the packed kernels take fewer if the handle says so,
-// and 8 (64 threads) for 8 slice pairs: measured at Ls = 16, 16 -> 8 sites per CTA (same warps
-// per SM, a finer last wave) took the FP32 hop from 56.4 to 55.9 us at 16^4 and from 842 to
-// 822 us at 32^4, FP16 from 589 to 580 us at 32^4, bit-identical.
+// slice in FP64), at most the half lattice; the packed kernels take fewer if the handle says so.
+// Packed kernels: 8 sites (64 threads) for 8 slice pairs: measured at Ls = 16, 16 -> 8 sites per
+// CTA (same warps per SM, a finer last wave) took the FP32 hop from 56.4 to 55.9 us at 16^4 and
+// from 842 to 822 us at 32^4, FP16 from 589 to 580 us at 32^4, bit-identical. Otherwise, where
+// one exists, the largest CTA of whole warps made of whole 4-site blocks: for 6 slice pairs
+// (Ls = 11-12) 16 sites (96 threads) instead of 21 (126) took the full-lattice FP32 hop at
+// 24^4 x 12 from 249 to 229 us, FP16 from 185 to 175 us, BF16 from 193 to 185 us (20 sites,
+// 120 threads: 244 / 189 / 197 us).
 int hop_sites_per_cta(const grid_dwf_t* h, int prec) {
   int spc = 128 / dhop_threads_per_site(prec, h->Ls);
-  if (prec != GRID_DWF_FP64 && ls_half(h->Ls) == 8) spc = 8;
+  if (prec != GRID_DWF_FP64) {
+    const int Lsh = ls_half(h->Ls);
+    if (Lsh == 8) {
+      spc = 8;
+    } else {
+      for (int s = spc - spc % 4; s >= 4; s -= 4)
+        if ((s * Lsh) % 32 == 0) {
+          spc = s;
+          break;
+        }
+    }
+  }
   if (prec != GRID_DWF_FP64 && h->spc > 0 && h->spc < spc) spc = h->spc;
   if (spc < 1) spc = 1;
   if (spc > h->g.N4h) spc = h->g.N4h;  // tiny lattices: one full CTA
@@ -250,13 +269,20 @@ int dhop_half(grid_dwf_t* h, int prec, const void* in, void* out, int out_parity
   a.zblk = 0;
   a.ctas_per_plane = 1;
   {
-    // Automatic choice (measured at 32^4 x 16, where the FP32 half field is 805 MB: lexicographic
-    // walk 988 us, z-blocks of 2 / 4 / 8 / 16 planes 920 / 859 / 833 / 868 us; no change at 16^4,
-    // whose fields stay in L2; the 16-bit kernels, bound by their arithmetic, gain nothing): blocks
-    // of 8 planes for FP32 fields larger than about 3/4 of L2.
+    // Automatic choice: an input t-plane is read again by the output planes t - 1 and t + 1, after
+    // about two t-planes of input, output and links have passed through L2. The FP32 kernel walks
+    // blocks of 8 (x, y) planes in z when that window exceeds half of L2 (32^4 x 16: 120 MB;
+    // lexicographic walk 988 us, z-blocks of 2 / 4 / 8 / 16 planes 920 / 859 / 833 / 868 us) and
+    // lexicographically otherwise (24^4 x 12: 40 MB, full-lattice hop 229 us against 240 us in
+    // z-blocks of 8; 16^4 x 16: no change). The 16-bit kernels, bound by their arithmetic, gain
+    // nothing.
     const int plane = h->g.Lxh * h->g.L[1];
     int zb = h->zblk;
-    if (zb < 0) zb = (prec == GRID_DWF_FP32 && half_bytes(h, prec) > ((size_t)96 << 20)) ? 8 : 0;
+    if (zb < 0) {
+      const size_t tplane = (size_t)plane * h->g.L[2];
+      const size_t window = 2 * tplane * ((size_t)ls_half(h->Ls) * 2 * 2 * 24 * 4 + 8 * 18 * 4);
+      zb = (prec == GRID_DWF_FP32 && window > h->l2_bytes / 2) ? 8 : 0;
+    }
     if (prec != GRID_DWF_FP64 && region.nsites == 0 && zb > 0 && zb < h->g.L[2] && h->g.L[2] % zb == 0 &&
         plane % a.sites_per_cta == 0) {
       a.zblk = zb;
@@ -276,7 +302,7 @@ int dhop_half(grid_dwf_t* h, int prec, const void* in, void* out, int out_parity
   int blocks = (h->g.N4h + a.sites_per_cta - 1) / a.sites_per_cta;
   const size_t rbytes = prec == GRID_DWF_FP64 ? 8 : 4;
   size_t smem = dhop_link_smem_bytes(prec, a.sites_per_cta, h->c12) +
-                (post != POST_NONE ? (size_t)a.sites_per_cta * h->Ls * 24 * rbytes : 0);
+                (post != POST_NONE ? (size_t)a.sites_per_cta * h->Ls * INV_SLICE_STRIDE * rbytes : 0);
   cudaError_t e;
   if (prec == GRID_DWF_FP64 && h->fp64_arith == GRID_DWF_FP64_ARITH_FLOAT_FLOAT) {
     smem = dhop_ff_smem_bytes(a.sites_per_cta, h->Ls, post != POST_NONE);
@@ -412,7 +438,16 @@ int grid_dwf_create(const int dims[4], int Ls, double M5, double mass, const int
   if (pdle) h->pdl = std::atoi(pdle) != 0;
   const char* lge = std::getenv("GRID_DWF_CG_LAG");
   if (lge) h->cg_lag = std::atoi(lge) > 0 ? 1 : 0;
+  const char* dle = std::getenv("GRID_DWF_CG_DELTA");
+  if (dle) {
+    const double d = std::atof(dle);
+    if (d > 0 && d < 1) h->cg_delta = d;
+  }
   cudaGetDevice(&h->device);
+  {
+    int l2 = 0;
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h->device) == cudaSuccess && l2 > 0) h->l2_bytes = (size_t)l2;
+  }
   cudaError_t e = cudaMalloc(&h->partials, sizeof(double) * 2 * RED_BLOCKS);
   if (e == cudaSuccess) e = cudaMalloc(&h->scal, sizeof(double) * S_COUNT);
   if (e == cudaSuccess) e = cudaMallocHost(&h->host_scal, sizeof(double) * (2 * S_COUNT + 1));
@@ -815,11 +850,14 @@ int cg_normal(grid_dwf_t* h, const void* rhs, void* xo_, double tol, int maxiter
     RET(ensure_gauge(h, PS));
     const double nreal = (double)N * Ls * 24;
     // Reliable update when the sloppy residual has dropped by delta since the last one. FP32
-    // inner solves keep their recursion accurate over three decades; with 16-bit storage the
-    // recursion drifts sooner (a smaller delta there adds iterations or stalls). Measured at
-    // 24^4 x 12 (1e-10): FP32 10 -> 4 FP64 Mpc^+ Mpc recomputations, 0.41 -> 0.32 s; FP16/BF16
-    // 10 -> 7.
-    const double delta = PS == GRID_DWF_FP32 ? 1e-3 : 0.03;
+    // inner solves keep their recursion accurate over four decades; with 16-bit storage the
+    // recursion drifts sooner (a smaller delta there adds iterations or stalls). Measured to a
+    // 1e-10 true residual: FP32 at 24^4 x 12, delta 1e-3 / 1e-4 / 1e-5: 4 / 3 / 3 FP64 Mpc^+ Mpc
+    // recomputations in 170 / 170 / 172 iterations, 0.235 / 0.220 / 0.222 s; at 32^4 x 16 (m =
+    // 0.005) 4 / 3 / 4 in 228 / 230 / 241 iterations, 1.013 / 0.961 / 1.054 s. FP16 at 24^4 x 12,
+    // delta 0.1 / 0.03 / 0.01 / 3e-3: 170 / 171 / 171 / 283 iterations, and at 1e-3 742; BF16 at
+    // 0.1 / 0.03 / 0.01: 197 / 223 / 381, and no convergence at 3e-3.
+    const double delta = h->cg_delta > 0 ? h->cg_delta : PS == GRID_DWF_FP32 ? 1e-4 : 0.03;
     double sigma = std::sqrt(nreal) / std::sqrt(rr);
     CK(launch_convert(P, GRID_DWF_FP32, r, rs, N, Ls, nullptr, sigma, h->stream), "cg init");
     CK(launch_convert(GRID_DWF_FP32, PS, rs, ps, N, Ls, nullptr, 1.0, h->stream), "cg init");

@@ -121,26 +121,26 @@ __device__ __forceinline__ void stage_link_ff(ff* dst, const char* src, bool neg
     }
 }
 
-// In-place inverse of the fifth-dimension matrix along one real of one site (stride 24 between
-// slices), the float-float form of mooee_inv_line.
+// In-place inverse of the fifth-dimension matrix along one real of one site (stride INV_SLICE_STRIDE
+// between slices), the float-float form of mooee_inv_line.
 __device__ __forceinline__ void mooee_inv_line_ff(ff* v, int Ls, bool forward_form, ff mass, ff inv_d, ff inv_den) {
   if (forward_form) {
     ff acc = ff_make(0.f, 0.f);
-    for (int k = 1; k < Ls; ++k) acc = ff_mul(ff_add<+1>(acc, v[k * 24]), inv_d);
+    for (int k = 1; k < Ls; ++k) acc = ff_mul(ff_add<+1>(acc, v[k * INV_SLICE_STRIDE]), inv_d);
     ff y = ff_mul(ff_add<-1>(v[0], ff_mul(mass, acc)), inv_den);
     v[0] = y;
     for (int s = 1; s < Ls; ++s) {
-      y = ff_mul(ff_add<+1>(v[s * 24], y), inv_d);
-      v[s * 24] = y;
+      y = ff_mul(ff_add<+1>(v[s * INV_SLICE_STRIDE], y), inv_d);
+      v[s * INV_SLICE_STRIDE] = y;
     }
   } else {
     ff acc = ff_make(0.f, 0.f);
-    for (int k = Ls - 2; k >= 0; --k) acc = ff_mul(ff_add<+1>(acc, v[k * 24]), inv_d);
-    ff y = ff_mul(ff_add<-1>(v[(Ls - 1) * 24], ff_mul(mass, acc)), inv_den);
-    v[(Ls - 1) * 24] = y;
+    for (int k = Ls - 2; k >= 0; --k) acc = ff_mul(ff_add<+1>(acc, v[k * INV_SLICE_STRIDE]), inv_d);
+    ff y = ff_mul(ff_add<-1>(v[(Ls - 1) * INV_SLICE_STRIDE], ff_mul(mass, acc)), inv_den);
+    v[(Ls - 1) * INV_SLICE_STRIDE] = y;
     for (int s = Ls - 2; s >= 0; --s) {
-      y = ff_mul(ff_add<+1>(v[s * 24], y), inv_d);
-      v[s * 24] = y;
+      y = ff_mul(ff_add<+1>(v[s * INV_SLICE_STRIDE], y), inv_d);
+      v[s * INV_SLICE_STRIDE] = y;
     }
   }
 }
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(128, DWF_FF_MIN_BLOCKS) dhop_kernel_ff(const _
   }
   ff* sm = reinterpret_cast<ff*>(smem_raw + (size_t)a.sites_per_cta * (FF_LINK_SITE_BYTES + 32) + FF_UH_BYTES);
   if (active && !pad) {
-    ff* dst = sm + ((size_t)site_local * Ls + s) * 24;
+    ff* dst = sm + ((size_t)site_local * Ls + s) * INV_SLICE_STRIDE;
 #pragma unroll
     for (int r = 0; r < 24; ++r) dst[r] = acc[r];
   }
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(128, DWF_FF_MIN_BLOCKS) dhop_kernel_ff(const _
       const int r = task - sl * 24;
       const bool upper = r < 12;
       const bool forward_form = (a.post == POST_INV) ? upper : !upper;
-      mooee_inv_line_ff(sm + (size_t)sl * Ls * 24 + r, Ls, forward_form, m, inv_d, inv_den);
+      mooee_inv_line_ff(sm + (size_t)sl * Ls * INV_SLICE_STRIDE + r, Ls, forward_form, m, inv_d, inv_den);
     }
   }
   __syncthreads();
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(128, DWF_FF_MIN_BLOCKS) dhop_kernel_ff(const _
     if (pad) {
       store_zero_slice<LSHC>(outb, s, Lsh);
     } else {
-      const ff* src = sm + ((size_t)site_local * Ls + s) * 24;
+      const ff* src = sm + ((size_t)site_local * Ls + s) * INV_SLICE_STRIDE;
 #pragma unroll
       for (int r = 0; r < 24; ++r) acc[r] = src[r];
       store_slice_ff<LSHC>(outb, s, Lsh, acc);
@@ -353,7 +353,7 @@ cudaError_t launch_ff_ls(const DhopArgs& a, bool dag, bool c12, int threads, int
 
 size_t dhop_ff_smem_bytes(int sites_per_cta, int Ls, bool post) {
   return (size_t)sites_per_cta * (FF_LINK_SITE_BYTES + 32) + FF_UH_BYTES +
-         (post ? (size_t)sites_per_cta * Ls * 24 * 8 : 0);
+         (post ? (size_t)sites_per_cta * Ls * INV_SLICE_STRIDE * 8 : 0);
 }
 
 cudaError_t launch_dhop_ff(const DhopArgs& a, bool dag, bool c12, int threads, int blocks, size_t smem,

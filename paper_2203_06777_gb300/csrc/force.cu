@@ -256,9 +256,9 @@ __global__ void __launch_bounds__(128) k_force(const Geom g, const char* psi, co
 //   - The link algebra of the site's four links (36 entries) is spread over the same lanes.
 // Rounding: the products of a slice pair and the sums over at most 16 pairs are FP32, as in the
 // general kernel (which flushes to FP64 after 8 pairs; here 16 pairs at most are summed in FP32).
-template <int LSH>
+template <int LSH, int THREADS = 128>
 struct ForceRegGeom {
-  static constexpr int SPC = 128 / LSH;                             // sites per CTA
+  static constexpr int SPC = THREADS / LSH;                         // sites per CTA
   static constexpr int PER_LANE = (18 + LSH - 1) / LSH;              // sum entries per lane after reduce-scatter
   static constexpr int NPAD = PER_LANE * LSH;                         // 18 reals padded to a multiple of LSH
   // B1 B2 per mu, U per mu, Y per mu, plus one float so that sites start in different banks
@@ -283,10 +283,11 @@ __device__ __forceinline__ void reduce_scatter(float (&v)[N], int lane_in_site) 
 // The own spinor of a term goes through shared memory and is read back per direction (128
 // registers, 4 CTAs per SM): holding it in 48 registers instead needed 168 registers, 3 CTAs per
 // SM and some spills, and measured 136 us against 111 us at 16^4 x 16.
-template <bool C12, int LSH>
-__global__ void __launch_bounds__(128, 4) k_force_reg(const Geom g, const char* psi, const char* chi, const char* Ue,
-                                                      const char* Uo, double* F, double* G, double coef) {
-  using GG = ForceRegGeom<LSH>;
+template <bool C12, int LSH, int THREADS = 128>
+__global__ void __launch_bounds__(THREADS, 512 / THREADS) k_force_reg(const Geom g, const char* psi, const char* chi,
+                                                                      const char* Ue, const char* Uo, double* F,
+                                                                      double* G, double coef) {
+  using GG = ForceRegGeom<LSH, THREADS>;
   constexpr int LB = link_bytes(4, C12);
   constexpr int SPC = GG::SPC, NPAD = GG::NPAD, PER_LANE = GG::PER_LANE;
   const size_t site_bytes = (size_t)LSH * 2 * 24 * 4;
@@ -307,7 +308,7 @@ __global__ void __launch_bounds__(128, 4) k_force_reg(const Geom g, const char* 
   __shared__ float ssm[SPC][GG::SITE_FLOATS];
   // the own site's spinor of the current term, one 16-byte vector per (chunk, thread): read back
   // for each direction's projection instead of being held in 48 registers
-  __shared__ float4 own_sm[12][128];
+  __shared__ float4 own_sm[12][THREADS];
   float* bs = ssm[site_local];          // [mu][term][18]
   float* us = bs + 4 * 36;              // [mu][18]
   float* ys = us + 4 * 18;              // [mu][18]
@@ -546,15 +547,18 @@ cudaError_t launch_force(int prec, bool c12, const Geom& g, const void* psi, con
   }
   const int Lsh = ls_half(g.Ls);
   if (prec == P32 && (Lsh == 8 || Lsh == 16)) {
-#define FR(L_)                                                                                           \
+    // CTAs of 64 threads for 8 pairs per site (8 sites; measured 108.2 us against 109.5 us with
+    // 128 threads at 16^4 x 16, the same warps per SM and a finer last wave), 128 for 16 pairs
+#define FR(L_, T_)                                                                                       \
   {                                                                                                      \
-    const dim3 gr((unsigned)(2 * ((g.N4h + ForceRegGeom<L_>::SPC - 1) / ForceRegGeom<L_>::SPC)));        \
+    constexpr int spc = ForceRegGeom<L_, T_>::SPC;                                                       \
+    const dim3 gr((unsigned)(2 * ((g.N4h + spc - 1) / spc)));                                            \
     if (c12)                                                                                             \
-      k_force_reg<true, L_><<<gr, 128, 0, st>>>(g, ps, ch, e, o, F, G, coef);                            \
+      k_force_reg<true, L_, T_><<<gr, T_, 0, st>>>(g, ps, ch, e, o, F, G, coef);                         \
     else                                                                                                 \
-      k_force_reg<false, L_><<<gr, 128, 0, st>>>(g, ps, ch, e, o, F, G, coef);                           \
+      k_force_reg<false, L_, T_><<<gr, T_, 0, st>>>(g, ps, ch, e, o, F, G, coef);                        \
   }
-    if (Lsh == 8) FR(8) else FR(16)
+    if (Lsh == 8) FR(8, 64) else FR(16, 128)
 #undef FR
     return cudaGetLastError();
   }

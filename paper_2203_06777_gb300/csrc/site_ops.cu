@@ -329,7 +329,8 @@ __global__ void __launch_bounds__(256) k_mooee(const void* in, void* out, long n
                                                bool inverse, double d5, double mass, double inv_d5, double inv_den) {
   using R = RT<P>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* sm = reinterpret_cast<R*>(smem_raw);  // [site][s < Ls][24]
+  R* sm = reinterpret_cast<R*>(smem_raw);  // [site][s < Ls][24 reals, padded to INV_SLICE_STRIDE]
+  constexpr int S = INV_SLICE_STRIDE;
   const int Lsh = ls_half(Ls);
   const long site0 = (long)blockIdx.x * spc;
   const int ns = (int)min((long)spc, nsites - site0);
@@ -344,7 +345,7 @@ __global__ void __launch_bounds__(256) k_mooee(const void* in, void* out, long n
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
       const int s = 2 * q + (i & 1);
-      if (s < Ls) sm[((size_t)sl * Ls + s) * 24 + 8 * g + (i >> 1)] = v[i];
+      if (s < Ls) sm[((size_t)sl * Ls + s) * S + 8 * g + (i >> 1)] = v[i];
     }
   }
   __syncthreads();
@@ -353,7 +354,7 @@ __global__ void __launch_bounds__(256) k_mooee(const void* in, void* out, long n
       const int sl = task / 24;
       const int r = task - sl * 24;
       const bool upper = r < 12;
-      mooee_inv_line<R>(sm + (size_t)sl * Ls * 24 + r, Ls, dag ? !upper : upper, R(mass), R(inv_d5), R(inv_den));
+      mooee_inv_line<R>(sm + (size_t)sl * Ls * S + r, Ls, dag ? !upper : upper, R(mass), R(inv_d5), R(inv_den));
     }
     __syncthreads();
     for (int u = threadIdx.x; u < units; u += blockDim.x) {
@@ -365,7 +366,7 @@ __global__ void __launch_bounds__(256) k_mooee(const void* in, void* out, long n
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const int s = 2 * q + (i & 1);
-        o[i] = s < Ls ? sm[((size_t)sl * Ls + s) * 24 + 8 * g + (i >> 1)] : R(0);
+        o[i] = s < Ls ? sm[((size_t)sl * Ls + s) * S + 8 * g + (i >> 1)] : R(0);
       }
       st_unit<P>(out, site0 + sl, g, q, Lsh, o);
     }
@@ -376,7 +377,7 @@ __global__ void __launch_bounds__(256) k_mooee(const void* in, void* out, long n
     const int q = u - rem * Lsh;
     const int sl = rem / 3;
     const int g = rem - sl * 3;
-    const R* base = sm + (size_t)sl * Ls * 24;
+    const R* base = sm + (size_t)sl * Ls * S;
     R o[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
@@ -391,7 +392,7 @@ __global__ void __launch_bounds__(256) k_mooee(const void* in, void* out, long n
       const int s_up = dag ? sp1 : sm1, s_lo = dag ? sm1 : sp1;
       const R c_up = dag ? cp : cm, c_lo = dag ? cm : cp;
       const bool upper = r < 12;
-      o[i] = R(d5) * base[s * 24 + r] + (upper ? c_up * base[s_up * 24 + r] : c_lo * base[s_lo * 24 + r]);
+      o[i] = R(d5) * base[s * S + r] + (upper ? c_up * base[s_up * S + r] : c_lo * base[s_lo * S + r]);
     }
     st_unit<P>(out, site0 + sl, g, q, Lsh, o);
   }
@@ -400,7 +401,7 @@ __global__ void __launch_bounds__(256) k_mooee(const void* in, void* out, long n
 cudaError_t launch_mooee(int prec, const void* in, void* out, long nsites, int Ls, bool dag, bool inverse, double d5,
                          double mass, double inv_d5, double inv_den, cudaStream_t st) {
   const size_t rbytes = prec == P64 ? 8 : 4;
-  const size_t site_smem = (size_t)Ls * 24 * rbytes;
+  const size_t site_smem = (size_t)Ls * INV_SLICE_STRIDE * rbytes;
   int spc = (int)((48 * 1024) / site_smem);
   if (spc > 64) spc = 64;
   if (spc < 1) return cudaErrorInvalidValue;
