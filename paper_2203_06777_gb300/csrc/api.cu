@@ -302,7 +302,9 @@ int dhop_half(grid_dwf_t* h, int prec, const void* in, void* out, int out_parity
   int blocks = (h->g.N4h + a.sites_per_cta - 1) / a.sites_per_cta;
   const size_t rbytes = prec == GRID_DWF_FP64 ? 8 : 4;
   size_t smem = dhop_link_smem_bytes(prec, a.sites_per_cta, h->c12) +
-                (post != POST_NONE ? (size_t)a.sites_per_cta * h->Ls * INV_SLICE_STRIDE * rbytes : 0);
+                (post == POST_NONE                ? 0
+                 : prec == GRID_DWF_FP64 ? (size_t)a.sites_per_cta * h->Ls * INV_SLICE_STRIDE * rbytes
+                                         : (size_t)a.sites_per_cta * inv_site_stride(h->Ls) * rbytes);
   cudaError_t e;
   if (prec == GRID_DWF_FP64 && h->fp64_arith == GRID_DWF_FP64_ARITH_FLOAT_FLOAT) {
     smem = dhop_ff_smem_bytes(a.sites_per_cta, h->Ls, post != POST_NONE);

@@ -675,9 +675,8 @@ constexpr int INV_SLICE_STRIDE = 25;
 // in shared memory with stride INV_SLICE_STRIDE between slices. FORWARD_FORM solves the chirality
 // coupled to s-1: y_0 = (b_0 - m sum_{k>=1} d^-(Ls-k) b_k) / (d + m d^-(Ls-1)),
 // y_s = (b_s + y_{s-1}) / d; otherwise the mirror image in s.
-template <typename R>
+template <typename R, int S = INV_SLICE_STRIDE>
 __device__ __forceinline__ void mooee_inv_line(R* v, int Ls, bool forward_form, R mass, R inv_d, R inv_den) {
-  constexpr int S = INV_SLICE_STRIDE;
   if (forward_form) {
     R acc = 0;
     for (int k = 1; k < Ls; ++k) acc = (acc + v[k * S]) * inv_d;
@@ -697,6 +696,62 @@ __device__ __forceinline__ void mooee_inv_line(R* v, int Ls, bool forward_form, 
       v[s * S] = y;
     }
   }
+}
+
+// The packed kernels stage the inverse differently: per site 24 lines, one per real component,
+// each holding the site's slices contiguously, so that a thread stores its two slices of a real
+// as one float2 and a line moves with 128-bit accesses. A line is padded to an odd number of
+// float4 (the eight lanes of a 128-bit access then cover all 32 banks), a site to a stride that
+// puts consecutive sites' float2 stores on consecutive banks.
+__host__ __device__ constexpr int inv_line_stride(int Ls) {
+  return (((Ls + 3) / 4) & 1) ? ((Ls + 3) & ~3) : ((Ls + 3) & ~3) + 4;
+}
+__host__ __device__ constexpr int inv_site_stride(int Ls) {
+  return 24 * inv_line_stride(Ls) +
+         ((((2 * ls_half(Ls) + 3) & ~3) - 24 * inv_line_stride(Ls)) % 32 + 32) % 32;
+}
+
+// mooee_inv_line on one contiguous line of LS slices (compile-time), held in registers between
+// one 128-bit load and one 128-bit store per four slices; the same operations in the same order.
+template <int LS>
+__device__ __forceinline__ void mooee_inv_line_vec(float* line, bool forward_form, float mass, float inv_d,
+                                                   float inv_den) {
+  constexpr int NV = (LS + 3) / 4;
+  float v[4 * NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    const float4 t = reinterpret_cast<const float4*>(line)[j];
+    v[4 * j] = t.x;
+    v[4 * j + 1] = t.y;
+    v[4 * j + 2] = t.z;
+    v[4 * j + 3] = t.w;
+  }
+  if (forward_form) {
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 1; k < LS; ++k) acc = (acc + v[k]) * inv_d;
+    float y = (v[0] - mass * acc) * inv_den;
+    v[0] = y;
+#pragma unroll
+    for (int s = 1; s < LS; ++s) {
+      y = (v[s] + y) * inv_d;
+      v[s] = y;
+    }
+  } else {
+    float acc = 0.f;
+#pragma unroll
+    for (int k = LS - 2; k >= 0; --k) acc = (acc + v[k]) * inv_d;
+    float y = (v[LS - 1] - mass * acc) * inv_den;
+    v[LS - 1] = y;
+#pragma unroll
+    for (int s = LS - 2; s >= 0; --s) {
+      y = (v[s] + y) * inv_d;
+      v[s] = y;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NV; ++j)
+    reinterpret_cast<float4*>(line)[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
 }
 
 // ---------------------------------------------------------------- kernel bodies
@@ -947,16 +1002,14 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
     return;
   }
   // Fifth-dimension inverse through shared memory (after the staged links): whole sites live in
-  // this CTA.
+  // this CTA, staged as lines (inv_site_stride / inv_line_stride; the pad slice of an odd Ls is
+  // stored past the line's end and never read).
   float* sm = reinterpret_cast<float*>(smem_raw + dhop_link_smem_bytes(P, a.sites_per_cta, false));
+  const int lst = inv_line_stride(Ls), sst = inv_site_stride(Ls);
   if (active) {
-    float* d0 = sm + ((size_t)site_local * Ls + 2 * q) * INV_SLICE_STRIDE;
+    float* d0 = sm + (size_t)site_local * sst + 2 * q;
 #pragma unroll
-    for (int r = 0; r < 24; ++r) d0[r] = acc[r].x;
-    if (!pad_lane) {
-#pragma unroll
-      for (int r = 0; r < 24; ++r) d0[INV_SLICE_STRIDE + r] = acc[r].y;
-    }
+    for (int r = 0; r < 24; ++r) *reinterpret_cast<float2*>(d0 + r * lst) = acc[r];
   }
   __syncthreads();
   const int nsites = a.sites_per_cta;
@@ -965,14 +1018,20 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
     const int r = task - sl * 24;
     const bool upper = r < 12;
     const bool forward_form = (a.post == POST_INV) ? upper : !upper;
-    mooee_inv_line<float>(sm + (size_t)sl * Ls * INV_SLICE_STRIDE + r, Ls, forward_form, (float)a.mass, (float)a.inv_d5,
-                          (float)a.inv_den);
+    float* line = sm + (size_t)sl * sst + r * lst;
+    if constexpr (LSC > 0)
+      mooee_inv_line_vec<LSC>(line, forward_form, (float)a.mass, (float)a.inv_d5, (float)a.inv_den);
+    else
+      mooee_inv_line<float, 1>(line, Ls, forward_form, (float)a.mass, (float)a.inv_d5, (float)a.inv_den);
   }
   __syncthreads();
   if (active) {
-    const float* s0 = sm + ((size_t)site_local * Ls + 2 * q) * INV_SLICE_STRIDE;
+    const float* s0 = sm + (size_t)site_local * sst + 2 * q;
 #pragma unroll
-    for (int r = 0; r < 24; ++r) acc[r] = make_float2(s0[r], pad_lane ? 0.f : s0[INV_SLICE_STRIDE + r]);
+    for (int r = 0; r < 24; ++r) {
+      const float2 v = *reinterpret_cast<const float2*>(s0 + r * lst);
+      acc[r] = make_float2(v.x, pad_lane ? 0.f : v.y);
+    }
     store_pair<P, LSHC>(outb, q, Lsh, acc);
   }
 }
