@@ -523,8 +523,9 @@ def profile_case(args):
     """A fixed, short launch sequence for a profiler (ncu), fields drawn on the device:
     --profile-kernel dhop: the full-lattice Dhop of one precision on the named workload, 3 warm-up
     calls then 3 more; force: the action and force (FP32 fields) likewise; cg: one mixed solve
-    (mode from --variants: f32, f16, bf16) to 1e-10. Prints one line with the CUDA-event time
-    (a number taken under a profiler is not a result)."""
+    (mode from --variants: f32, f16, bf16) to 1e-10; mpc: a half-lattice DhopEO three times, then
+    Mpc (its two launches, with the fused fifth-dimension epilogues) three times. Prints one line
+    with the CUDA-event time (a number taken under a profiler is not a result)."""
     import torch
 
     from paper_2203_06777_gb300 import dwf
@@ -561,6 +562,26 @@ def profile_case(args):
         return
     prec = {"f32": dwf.FP32, "f16": dwf.FP16, "bf16": dwf.BF16, "f64": dwf.FP64, "f64ff": dwf.FP64}[args.variants.split(",")[0]]
     dev = torch.device("cuda")
+    if args.profile_kernel == "mpc":
+        op = dwf.GridDWF(dims, Ls, spec["M5"], spec["mass"], bc=BC)
+        op.set_gauge(synth.random_gauge_device(dims, 1000 * spec["case"], spec["eps"] or 0.3, dev))
+        half = op.pack(synth.random_spinor_device(dims, Ls, 1000 * spec["case"] + 1, dev), prec, dwf.ODD)
+        out, te = torch.empty_like(half), torch.empty_like(half)
+        torch.cuda.empty_cache()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        for _ in range(3):
+            op.dhop(half, dwf.EVEN, out=out)
+        e1.record()
+        for _ in range(3):
+            op.mpc(half, out=out, tmp_even=te)
+        e2.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": args.profile, "kernel": "mpc", "variant": args.variants.split(",")[0],
+                          "us_per_dhop_half": round(e0.elapsed_time(e1) * 1e3 / 3, 2),
+                          "us_per_mpc": round(e1.elapsed_time(e2) * 1e3 / 3, 2)}), flush=True)
+        op.close()
+        return
     op = dwf.GridDWF(dims, Ls, spec["M5"], spec["mass"], bc=BC,
                      fp64_arith=dwf.FP64_ARITH_FLOAT_FLOAT if args.variants.startswith("f64ff") else 0)
     op.set_gauge(synth.random_gauge_device(dims, 1000 * spec["case"], spec["eps"] or 0.3, dev))
@@ -798,8 +819,9 @@ def main(argv=None):
     ap.add_argument("--no-force", action="store_true", help="skip the action/force and pseudofermion force timing")
     ap.add_argument("--profile", default=None, help="run only a short launch sequence of this workload "
                     "(a synth.WORKLOADS name) for a profiler, in the first precision of --variants")
-    ap.add_argument("--profile-kernel", default="dhop", choices=["dhop", "force", "cg"],
-                    help="what --profile runs: the hopping term, the action and force, or one mixed CG solve")
+    ap.add_argument("--profile-kernel", default="dhop", choices=["dhop", "force", "cg", "mpc"],
+                    help="what --profile runs: the hopping term, the action and force, one mixed CG solve, "
+                    "or a half-lattice hop and Mpc")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
