@@ -417,7 +417,7 @@ def run_force(dwf, torch, spec, reps=20):
     return {"workload": "dwf_16x16x16x16_ls16_haar", "ms_per_force": round(ms, 4), "reps": reps,
             "precision": "fp32 fields, fp64 accumulation across blocks of 8 slice pairs",
             "ms_per_force_fp64": round(ms64, 4), "ms_per_force_fp64_float_float": round(ms64ff, 4),
-            "includes": "M psi (one launch: Dhop with the fused Mooee term, both halves), |M psi|^2, force and ambient-gradient kernel"}
+            "includes": "M psi with |M psi|^2 summed in the same launch (Dhop with the fused Mooee term and norm, both halves), a one-CTA sum of the partials, force and ambient-gradient kernel"}
 
 
 def run_pf_force(dwf, torch, spec):

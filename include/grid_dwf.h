@@ -196,7 +196,9 @@ int grid_dwf_cg(grid_dwf_t* h, const void* b, void* x, double tol, int maxiter, 
  * Reading: with chi = M psi, the link derivative of S = |M psi|^2 comes from the hopping term
  * alone, per link an outer product of psi and the spin-projected chi summed over s and spin;
  * F = TA(G U^+) under U -> exp(eps A) U, TA the traceless anti-Hermitian part; FP32 fields
- * accumulate in FP32 within blocks of 16 slices and in FP64 across blocks.
+ * accumulate in FP32 within blocks of 16 slices and in FP64 across blocks; with FP32 fields and
+ * 18-real links |M psi|^2 is summed in the launch that forms M psi (FP32 within a thread's slice
+ * pair, FP64 across CTAs).
  * S = |M psi|^2 for a full field psi (FP64 or FP32), its su(3) force F and ambient gradient
  * G = dS/dRe U + i dS/dIm U, both canonical gauge layout FP64 device buffers (either may be
  * NULL). chi: full field of the same precision receiving M psi, or NULL for handle-owned

@@ -103,7 +103,7 @@ enum WsId : int {
   WS_CG_RED,
 };
 
-// Optional CG epilogue of a packed half-lattice hop (see dhop_kernel.cuh): per-CTA partial sums
+// Optional CG epilogue of a packed hop (see dhop_kernel.cuh): per-CTA partial sums
 // into red; with r, the update r -= (*coef) * result instead of a stored result.
 struct CgEpilogue {
   double* red = nullptr;
@@ -325,14 +325,22 @@ int dhop_half(grid_dwf_t* h, int prec, const void* in, void* out, int out_parity
 // Both halves of a full-lattice hop (each output half from the other input half, independent):
 // one launch for the packed precisions (one ramp-up and tail instead of two), two for FP64.
 int dhop_full(grid_dwf_t* h, int prec, const char* in, char* out, bool dag, int pre, double alpha, double beta,
-              const char* aux) {
+              const char* aux, const CgEpilogue& epi = CgEpilogue()) {
   const size_t hb = half_bytes(h, prec);
   if (prec == GRID_DWF_FP64) {
     RET(dhop_half(h, prec, in + hb, out, 0, dag, pre, POST_NONE, alpha, beta, aux));
     return dhop_half(h, prec, in, out + hb, 1, dag, pre, POST_NONE, alpha, beta, aux ? aux + hb : nullptr);
   }
   return dhop_half(h, prec, in + hb, out, 0, dag, pre, POST_NONE, alpha, beta, aux, in, out + hb,
-                   aux ? aux + hb : nullptr);
+                   aux ? aux + hb : nullptr, epi);
+}
+
+// Partial sums of a packed full-lattice launch with the norm epilogue: one per full CTA of
+// either half, and one per half for the end CTAs of a ragged lattice.
+int full_partials(const grid_dwf_t* h, int prec) {
+  const int spc = hop_sites_per_cta(h, prec);
+  const long N = h->g.N4h;
+  return (int)(2 * (N / spc) + (N % spc ? 2 : 0));
 }
 
 // out_o = Mpc in_o (dag: Mpc^+), via t_e = Mooee^-1 D_eo in and out = Mooee in - D_oe t_e / 4.
@@ -1053,9 +1061,21 @@ int grid_dwf_force(grid_dwf_t* h, int precision, const void* psi, void* chi, dou
   const size_t gb = (size_t)h->g.N4h * 2 * 4 * 18 * sizeof(double);
   if (F && (overlap(F, gb, psi, fb) || overlap(F, gb, c, fb))) return fail(h, GRID_DWF_ERR_ALIAS, "force: F overlaps");
   if (G && (overlap(G, gb, psi, fb) || overlap(G, gb, c, fb))) return fail(h, GRID_DWF_ERR_ALIAS, "force: G overlaps");
-  RET(grid_dwf_m(h, precision, psi, c, 0));
-  CK(launch_reduce(precision, c, nullptr, 2L * h->g.N4h, h->Ls, h->partials, h->scal, FIN_STORE, S_TMP0, h->stream),
-     "force action");
+  if (precision == GRID_DWF_FP32 && !h->c12) {
+    // chi = M psi with |chi|^2 summed in the same launch (one partial per CTA, FP64 across CTAs)
+    const int nred = full_partials(h, precision);
+    void* rp = nullptr;
+    RET(ws_get(h, WS_CG_RED, sizeof(double) * (size_t)nred, &rp));
+    CgEpilogue norm;
+    norm.red = static_cast<double*>(rp);
+    const char* ic = static_cast<const char*>(psi);
+    RET(dhop_full(h, precision, ic, static_cast<char*>(c), false, PRE_MOOEE, -0.5, 1.0, ic, norm));
+    CK(launch_finalize_n(norm.red, nred, h->scal, FIN_STORE, S_TMP0, h->stream), "force action");
+  } else {
+    RET(grid_dwf_m(h, precision, psi, c, 0));
+    CK(launch_reduce(precision, c, nullptr, 2L * h->g.N4h, h->Ls, h->partials, h->scal, FIN_STORE, S_TMP0, h->stream),
+       "force action");
+  }
   RET(ensure_gauge(h, precision));
   if (F || G)
     CK(launch_force(precision, h->c12, h->g, psi, c, h->gauge[precision][0], h->gauge[precision][1], F, G, 1.0, h->fp64_arith == GRID_DWF_FP64_ARITH_FLOAT_FLOAT,

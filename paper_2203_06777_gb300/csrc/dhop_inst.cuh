@@ -21,8 +21,8 @@ static cudaError_t launch_one(const DhopArgs& a, int threads, int blocks, size_t
     // full CTAs only (the packed kernel has no tail handling); a ragged end gets one more CTA (per
     // half) flush with the end of the lattice, launched after the first so no two writes overlap
     // in time. a.in2 != nullptr: both halves of a full-lattice hop in the same launches.
-    // CG epilogues: partial sums [0, full) from the full CTAs, [full] from the end CTA, which adds
-    // only the sites the full CTAs did not cover.
+    // CG epilogues: partial sums [0, halves * full) from the full CTAs (CTA order), then one per
+    // half from the end CTAs, which add only the sites the full CTAs did not cover.
     const int nsites = a.region_sites > 0 ? a.region_sites : a.g.N4h;
     const int full = nsites / a.sites_per_cta;
     const int halves = a.in2 ? 2 : 1;
@@ -52,7 +52,7 @@ static cudaError_t launch_one(const DhopArgs& a, int threads, int blocks, size_t
       DhopArgs t = a;
       t.site_base = a.g.N4h - a.sites_per_cta;
       t.blocks1 = 1;
-      t.red_base = full;
+      t.red_base = halves * full;
       t.own_from = full * a.sites_per_cta;
       kern<<<halves, threads, smem, stream>>>(t);
     }

@@ -766,7 +766,8 @@ __device__ __forceinline__ void mooee_inv_line_vec(float* line, bool forward_for
 //                 equals p^+ Mpc^+ Mpc p) to the launch's per-CTA partial sums;
 //   EPI_AXPY (8): do not store the result; update the FP32 field r -= c * result with c read from
 //                 device memory (the CG step length), and add |r|^2 to the partial sums.
-// Neither is combined with a post-operation or with a full-lattice launch.
+// Neither is combined with a post-operation; EPI_NORM also serves full-lattice launches (one
+// partial per CTA of either half), EPI_AXPY only half-lattice ones.
 //   EPI_HALO (16): the lattice is one block of a lattice split in t (see DhopArgs): hops that leave
 //                 the block in t take the neighbours' projected faces; launched over the face
 //                 planes only (the interior needs no halo and runs the plain instantiation).
@@ -995,7 +996,7 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
 #pragma unroll
         for (int r = 0; r < 24; ++r) n2 = fmaf(acc[r].x, acc[r].x, fmaf(acc[r].y, acc[r].y, n2));
       }
-      cta_sum_to(owned ? (double)n2 : 0.0, a.red + a.red_base + bid);
+      cta_sum_to(owned ? (double)n2 : 0.0, a.red + a.red_base + (int)blockIdx.x);
     } else {
       store_pair<P, LSHC>(outb, q, Lsh, acc);
     }
