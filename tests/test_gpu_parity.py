@@ -207,7 +207,11 @@ def test_mooee_family(dwf, oracle_lib, Ls, prec):
     assert rel(host(op.unpack(g)), oracle_lib.mooee(dims, Ls, M5, MASS, psi_r, inverse=True)) < TOL[prec]
 
 
-@pytest.mark.parametrize("dims,Ls", [((4, 4, 4, 4), 8), ((2, 4, 6, 4), 5), ((6, 4, 2, 2), 12)])
+# The packed kernels' CTA sizes: Ls 5-6 take 32 sites of 3 slice pairs (96 threads; 48 sites per
+# parity here, so one end CTA), Ls 11-12 16 sites of 6, Ls 23-24 8 sites of 12, which also sets the
+# Mooee^-1 lines' strides (28 and 696 floats at Ls = 24).
+@pytest.mark.parametrize("dims,Ls", [((4, 4, 4, 4), 8), ((2, 4, 6, 4), 5), ((6, 4, 2, 2), 12), ((4, 2, 2, 6), 6),
+                                     ((4, 4, 2, 2), 24)])
 @pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_m_mpc_mdagm(dwf, oracle_lib, dims, Ls, prec):
     op, U = make(dwf, dims, Ls, 61)
