@@ -261,8 +261,11 @@ struct ForceRegGeom {
   static constexpr int SPC = THREADS / LSH;                         // sites per CTA
   static constexpr int PER_LANE = (18 + LSH - 1) / LSH;              // sum entries per lane after reduce-scatter
   static constexpr int NPAD = PER_LANE * LSH;                         // 18 reals padded to a multiple of LSH
-  // B1 B2 per mu, U per mu, Y per mu, plus one float so that sites start in different banks
-  static constexpr int SITE_FLOATS = 4 * 36 + 4 * 18 + 4 * 18 + 1;
+  // B1 B2 per mu, U per mu, Y per mu, padded so that the sites of a warp fall on different banks:
+  // 299 floats give the fewest conflicts of the strides 289-329 over the partial-sum stores and the
+  // link algebra's reads of 8-lane sites (53 extra wavefronts per warp against 116 at 289, by
+  // simulation; 16-lane sites are indifferent)
+  static constexpr int SITE_FLOATS = 4 * 36 + 4 * 18 + 4 * 18 + 11;
 };
 
 template <int N, int LSH>
