@@ -268,6 +268,7 @@ int dhop_half(grid_dwf_t* h, int prec, const void* in, void* out, int out_parity
   a.site_base = region.site_base;
   a.zblk = 0;
   a.ctas_per_plane = 1;
+  a.interleave = 0;
   {
     // Automatic choice: an input t-plane is read again by the output planes t - 1 and t + 1, after
     // about two t-planes of input, output and links have passed through L2. The FP32 kernel walks
@@ -277,12 +278,19 @@ int dhop_half(grid_dwf_t* h, int prec, const void* in, void* out, int out_parity
     // z-blocks of 8; 16^4 x 16: no change). The 16-bit kernels, bound by their arithmetic, gain
     // nothing.
     const int plane = h->g.Lxh * h->g.L[1];
+    const size_t tplane = (size_t)plane * h->g.L[2];
     int zb = h->zblk;
     if (zb < 0) {
-      const size_t tplane = (size_t)plane * h->g.L[2];
       const size_t window = 2 * tplane * ((size_t)ls_half(h->Ls) * 2 * 2 * 24 * 4 + 8 * 18 * 4);
       zb = (prec == GRID_DWF_FP32 && window > h->l2_bytes / 2) ? 8 : 0;
     }
+    // FP32: both halves of a full-lattice launch in alternating CTAs when the reuse windows of both
+    // fit in half of L2 together (the halves then share their link reads there): 16^4 x 16 55.3 ->
+    // 54.2 us; where they do not fit it costs 4-8% (24^4 x 12 227 -> 236 us, 32^4 x 16 817 ->
+    // 862 us, FP16 at 32^4 586 -> 634 us), and FP16 / BF16 at 16^4 gain nothing, so it is chosen
+    // for FP32 below that size only.
+    const size_t window_p = 2 * tplane * ((size_t)ls_half(h->Ls) * 2 * 2 * 24 * 4 + 8 * 18 * 4);
+    a.interleave = (prec == GRID_DWF_FP32 && in2 != nullptr && 2 * window_p <= h->l2_bytes / 2) ? 1 : 0;
     if (prec != GRID_DWF_FP64 && region.nsites == 0 && zb > 0 && zb < h->g.L[2] && h->g.L[2] % zb == 0 &&
         plane % a.sites_per_cta == 0) {
       a.zblk = zb;

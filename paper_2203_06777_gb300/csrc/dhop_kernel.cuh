@@ -83,6 +83,9 @@ struct DhopArgs {
   // Requires full CTAs tiling each (x, y) plane: ctas_per_plane * sites_per_cta = Lx/2 * Ly.
   int zblk, ctas_per_plane;
   FastDiv div_cpp, div_zblk, div_lt;
+  // Full-lattice launches: 1 to alternate the CTAs between the two halves (CTA 2b + h: CTA b of
+  // half h) instead of running all CTAs of the first half first.
+  int interleave;
   double alpha, beta;
   double d5;       // 5 - M5
   double mass;     // m
@@ -806,8 +809,10 @@ __device__ __forceinline__ void dhop_body_pair(const DhopArgs& a) {
   // one-CTA launch whose site_base places it flush with the end (it rewrites a few sites with the
   // same values). The kernel then has no tail handling at all: a per-thread guard around the hop
   // loop, or a clamped site index, measured 5-10% slower.
-  const bool second = (int)blockIdx.x >= a.blocks1;  // the other half of a full-lattice launch
-  const int bid = second ? (int)blockIdx.x - a.blocks1 : (int)blockIdx.x;
+  // the other half of a full-lattice launch: CTAs [blocks1, 2 blocks1), or, with interleave,
+  // the odd CTAs (the halves then read the same links at about the same time)
+  const bool second = a.interleave ? ((int)blockIdx.x & 1) != 0 : (int)blockIdx.x >= a.blocks1;
+  const int bid = a.interleave ? (int)blockIdx.x >> 1 : second ? (int)blockIdx.x - a.blocks1 : (int)blockIdx.x;
   const int out_parity = second ? 1 - a.out_parity : a.out_parity;
   int cta = bid;
   if (a.zblk > 0) {  // plane w = zi + zblk * (t + Lt * zb) of the walk is the lattice's plane z + Lz * t
