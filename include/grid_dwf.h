@@ -88,9 +88,12 @@ typedef struct {
  * third rebuilt as the conjugated cross product, exact for SU(3) links); stream is a
  * cudaStream_t (NULL = legacy default stream). Uses the current CUDA device. On success *out
  * owns device memory for the links and workspaces, freed by grid_dwf_destroy.
- * Tuning read from the environment at create (results are the same bit for bit; only the speed
- * changes): GRID_DWF_ZBLOCK (CTA walk of the FP32/FP16/BF16 hops in blocks of that many z-planes;
- * default: 8 for FP32 fields larger than ~96 MB, else the lexicographic walk, 0), GRID_DWF_PDL
+ * Tuning read from the environment at create (the operators' results are the same bit for bit
+ * and only the speed changes, except that sums over the lattice formed inside a hop, the fused
+ * CG's p^+ A p and |r|^2 and the force's action, group their per-CTA partial sums differently):
+ * GRID_DWF_ZBLOCK (CTA walk of the FP32/FP16/BF16 hops in blocks of that many z-planes; default:
+ * 8 for FP32 when two t-planes of input, output and links exceed half of L2, else the
+ * lexicographic walk, 0), GRID_DWF_PDL
  * (0 disables launching those hops as programmatic dependents of the previous kernel; default 1),
  * GRID_DWF_SITES_PER_CTA (fewer sites per CTA than fill 128 threads), GRID_DWF_SYNC_DEBUG (1:
  * synchronise after every call to surface asynchronous errors at their call). GRID_DWF_CG_LAG (0 or

@@ -47,9 +47,9 @@ struct DhopArgs {
   int sites_per_cta;  // whole sites per CTA
   int pre, post;
   int site_base;      // packed kernels: first site of block 0 (every CTA of a launch is full)
-  // Packed kernels, both halves of a full-lattice hop in one launch: CTAs from blocks1 on apply the
-  // other half (output parity 1 - out_parity, fields in2 / out2 / aux2, links swapped). A launch
-  // of one half sets blocks1 to its grid size.
+  // Packed kernels, both halves of a full-lattice hop in one launch: CTAs from blocks1 on (or the
+  // odd CTAs, with interleave below) apply the other half (output parity 1 - out_parity, fields
+  // in2 / out2 / aux2, links swapped). A launch of one half sets blocks1 to its grid size.
   int blocks1;
   const void* in2;
   void* out2;
