@@ -97,9 +97,10 @@ def measured_traffic(profile=TRAFFIC_PROFILE):
         return None
 
 
-def algorithmic_bytes_per_site(real_bytes: int, Ls: int) -> float:
-    """Each input spinor read once, each output written once, 8 links per 4D site amortised over Ls."""
-    return real_bytes * (24 + 24) + 8 * 18 * real_bytes / Ls
+def algorithmic_bytes_per_site(real_bytes: int, Ls: int, link_reals: int = 18) -> float:
+    """Each input spinor read once, each output written once, 8 links per 4D site amortised over Ls
+    (18 reals each, or 12 with compressed links)."""
+    return real_bytes * (24 + 24) + 8 * link_reals * real_bytes / Ls
 
 
 # ---------------------------------------------------------------- clocks
@@ -211,12 +212,12 @@ def barrier(world: int):
 # ---------------------------------------------------------------- GPU arm
 
 
-def make_sets(dwf, torch, spec, prec, nsets, seed0, fp64_arith=0):
+def make_sets(dwf, torch, spec, prec, nsets, seed0, fp64_arith=0, compress12=False):
     dims, Ls = spec["dims"], spec["Ls"]
     sets = []
     for k in range(nsets):
         U = synth.random_gauge(dims, seed=1000 * spec["case"] + seed0 + 10 * k, eps=spec["eps"])
-        op = dwf.GridDWF(dims, Ls, spec["M5"], spec["mass"], bc=BC, fp64_arith=fp64_arith)
+        op = dwf.GridDWF(dims, Ls, spec["M5"], spec["mass"], bc=BC, fp64_arith=fp64_arith, compress12=compress12)
         op.set_gauge(torch.from_numpy(U).cuda())
         psi = synth.random_spinor(dims, Ls, seed=1000 * spec["case"] + seed0 + 10 * k + 1)
         src = op.pack(torch.from_numpy(psi).cuda(), prec, dwf.FULL)
@@ -234,7 +235,12 @@ def launches_per_step(op, prec, dwf) -> int:
     if prec == dwf.FP64:
         return 2
     lsh = (op.Ls + 1) // 2
-    spc = min(max(1, 8 if lsh == 8 else 128 // lsh), op.half_sites)
+    spc = 128 // lsh
+    if lsh == 8:
+        spc = 8
+    else:  # the largest CTA of whole warps made of whole 4-site blocks, where one exists
+        spc = next((s for s in range(spc - spc % 4, 3, -4) if (s * lsh) % 32 == 0), spc)
+    spc = min(max(1, spc), op.half_sites)
     return 1 if op.half_sites % spc == 0 else 2
 
 
@@ -650,12 +656,13 @@ def gpu_arm(args):
     clocks = None
     e2e = None
     wanted = args.variants.split(",")
-    for name, prec, rb in (("f32", dwf.FP32, 4), ("f64", dwf.FP64, 8), ("f64ff", dwf.FP64, 8), ("f16", dwf.FP16, 2),
-                           ("bf16", dwf.BF16, 2)):
+    for name, prec, rb in (("f32", dwf.FP32, 4), ("f32c12", dwf.FP32, 4), ("f64", dwf.FP64, 8), ("f64ff", dwf.FP64, 8),
+                           ("f16", dwf.FP16, 2), ("bf16", dwf.BF16, 2)):
         if name not in wanted:
             continue
         arith = dwf.FP64_ARITH_FLOAT_FLOAT if name == "f64ff" else dwf.FP64_ARITH_NATIVE
-        sets = make_sets(dwf, torch, spec, prec, 3, seed0=0, fp64_arith=arith)
+        c12 = name == "f32c12"
+        sets = make_sets(dwf, torch, spec, prec, 3, seed0=0, fp64_arith=arith, compress12=c12)
         steps = args.steps
         if name == "f32":
             with ClockSampler(torch.cuda.current_device()) as cs:
@@ -674,7 +681,7 @@ def gpu_arm(args):
         secs = reduce_max(secs, world)
         launches = steps * launches_per_step(sets[0][0], prec, dwf)
         per_step = secs / steps
-        bytes_site = algorithmic_bytes_per_site(rb, Ls)
+        bytes_site = algorithmic_bytes_per_site(rb, Ls, 12 if c12 else 18)
         gbs = bytes_site * 2 * n5 / per_step / 1e9
         gflops = FLOPS_PER_SITE * 2 * n5 / per_step / 1e9
         rec = {"gflops": round(gflops, 1), "algorithmic_gbs": round(gbs, 1),
@@ -686,6 +693,9 @@ def gpu_arm(args):
             rec["bound"] = "alu"
             rec["alu_peak_gflops"] = peaks_alu["fp64_fma_gflops"]
             rec["alu_peak_kind"] = "measured (grid_dwf_pipe_peak, FP64 FMA)"
+        if c12:
+            rec["links"] = "12 reals per link (third row rebuilt as the conjugated cross product)"
+            rec["speedup_vs_f32"] = round(variants["f32"]["us_per_step"] / rec["us_per_step"], 3) if "f32" in variants else None
         if name == "f64ff":
             rec["arithmetic"] = "float-float (FP64 storage, pairs of FP32 numbers, ~46 significant bits)"
             rec["bound"] = "instruction issue (FP32, integer and FP64 pipes)"
@@ -808,7 +818,8 @@ def main(argv=None):
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=20)
-    ap.add_argument("--variants", default="f32,f64,f64ff,f16,bf16", help="comma list of f32,f64,f64ff,f16,bf16")
+    ap.add_argument("--variants", default="f32,f32c12,f64,f64ff,f16,bf16",
+                    help="comma list of f32,f32c12 (FP32 with 12-real links),f64,f64ff,f16,bf16")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cg", action="store_true", help="skip the CG time-to-solution comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
