@@ -256,6 +256,15 @@ def soak(dwf, torch, sets, seconds):
         torch.cuda.synchronize()
 
 
+def hold_stream(torch, stream, us=150):
+    """Keep `stream` busy for about `us` microseconds (torch's bounded clock-spin kernel) so that the
+    host has queued the first timed launches when the start event is reached: the timed region
+    then holds the K steps back to back, not the host's latency to issue the first one."""
+    if hasattr(torch.cuda, "_sleep"):
+        with torch.cuda.stream(stream):
+            torch.cuda._sleep(int(us * 2000))  # ~2 GHz SM clock
+
+
 def time_dhop(dwf, torch, sets, steps, warmup, world):
     """Time `steps` full-lattice Dhop applications (DhopEO + DhopOE, one call each) with CUDA events."""
     stream = torch.cuda.current_stream()
@@ -270,6 +279,7 @@ def time_dhop(dwf, torch, sets, steps, warmup, world):
     barrier(world)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    hold_stream(torch, stream)
     e0.record(stream)
     for i in range(steps):
         step(warmup + i)
@@ -476,6 +486,7 @@ def run_sweep32(dwf, torch, steps=20, warmup=3, fp64_peak=None):
             op.dhop(src, dwf.FULL, out=dst)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        hold_stream(torch, stream)
         e0.record(stream)
         for _ in range(n):
             op.dhop(src, dwf.FULL, out=dst)
