@@ -143,7 +143,7 @@ int grid_dwf_convert(grid_dwf_t* h, int src_precision, int dst_precision, int su
 /* Hopping term. parity GRID_DWF_EVEN: out (even half) = DhopEO in (odd half); GRID_DWF_ODD:
  * out (odd) = DhopOE in (even); GRID_DWF_FULL: full fields, both halves. dag != 0: Dhop^+.
  * 1320 flops per output 5D site.
- * Source: the "main kernel DWF code" of the paper's Section 3 (Nsight-Compute figure: about 80%
+ * Source: the main DWF kernel profiled in the paper's Section 3 (Nsight-Compute figure: about 80%
  * of peak memory bandwidth, 39% of the floating-point pipe) and the Conclusion's node-local
  * "Wilson" matrix; the paper prints no formula, so the definition is the Dhop formula above
  * (chiral gamma basis, (1 - gamma_mu) on the forward hop, bc[mu] on hops crossing the edge). */
@@ -151,7 +151,7 @@ int grid_dwf_dhop(grid_dwf_t* h, int precision, const void* in, void* out, int p
 
 /* Fifth-dimension operator on a field of `subset`: Mooee, Mooee^+ (dag), Mooee^-1 (inverse) or
  * (Mooee^+)^-1. In-place use (in == out) is allowed.
- * Source: one of "all kernels involved in the DWF Dirac operator" of the paper's Conclusion and
+ * Source: one of the kernels of the DWF Dirac operator sequence in the paper's Conclusion and
  * Section 3 (Nsight-Systems figure); no formula is printed, so this is the Shamir term of the
  * preamble: (5 - M5) on the diagonal, P- coupling s to s+1 and P+ coupling s to s-1 with +m on
  * the wrap-around; Mooee^+ is its transpose in s, Mooee^-1 the closed-form inverse of the cyclic

@@ -7,7 +7,7 @@
  * the library never calls it.
  *
  * What the paper fixes and what it leaves open. The paper (Introduction; Section 3, the
- * Nsight-Compute profile of "the main kernel DWF code" and the Conclusion's node-local
+ * Nsight-Compute profile of its main DWF kernel and the Conclusion's node-local
  * "Wilson" matrix) names the domain wall fermion Dirac operator and its Wilson hopping kernel
  * as the memory-bound hot path, but prints no formula for them. The oracle therefore writes
  * out the standard Shamir operator, with these readings:

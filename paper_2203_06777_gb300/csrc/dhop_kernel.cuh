@@ -1,7 +1,7 @@
 // The Wilson hopping stencil on 5D domain-wall fields (DhopEO / DhopOE and their adjoints),
 // with optional fused fifth-dimension epilogues.
 //
-// The paper (Section 3, the Nsight-Compute profile of "the main kernel DWF code"; Conclusion,
+// The paper (Section 3, the Nsight-Compute profile of its main DWF kernel; Conclusion,
 // the node-local "Wilson" matrix) identifies this stencil as the memory-bound hot path of the
 // domain wall fermion operator. For output sites x of one parity and every slice s:
 //
