@@ -71,12 +71,18 @@ TRAFFIC_PROFILE_32 = "profiles/dhop_fp32_32x32x32x32_ls16.md"
 
 
 def kernel_source_hash() -> str:
+    """Hash of the FP32 hop's sources with their comments removed (a capture stays valid while the
+    code it measured is unchanged)."""
     import hashlib
+    import re
 
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update(re.sub(r"[ \t]+\n", "\n", text).encode())
     return h.hexdigest()[:16]
 
 
