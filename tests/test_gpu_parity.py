@@ -286,6 +286,30 @@ def test_cg_solves_full_system(dwf, oracle_lib, mode):
     assert rel(xs, xo) < 1e-7
 
 
+@pytest.mark.parametrize("mode,delta,lag", [(1, "0.1", "0"), (1, "1e-6", "1"), (2, "0.3", "1"), (3, "0.01", "1"),
+                                            (2, None, "0")])
+def test_mixed_cg_tuning_knobs(dwf, oracle_lib, monkeypatch, mode, delta, lag):
+    """GRID_DWF_CG_DELTA and GRID_DWF_CG_LAG (read when the handle is created) change how often
+    the mixed CG folds its inner solution into x and recomputes the FP64 residual, and when it
+    decides to, not what it converges to: the solution still reaches the tolerance, and the
+    oracle's recomputed residual of the full system agrees."""
+    if delta is None:
+        monkeypatch.delenv("GRID_DWF_CG_DELTA", raising=False)
+    else:
+        monkeypatch.setenv("GRID_DWF_CG_DELTA", delta)
+    monkeypatch.setenv("GRID_DWF_CG_LAG", lag)
+    dims, Ls = (4, 4, 4, 4), 8
+    op, U = make(dwf, dims, Ls, 93, eps=0.4)
+    b = synth.random_spinor(dims, Ls, seed=94)
+    fb = op.pack(dev(b), 0, dwf.FULL)
+    x, st = op.cg(fb, tol=1e-10, maxiter=5000, mode=mode)
+    assert st.converged and st.true_residual <= 1e-10
+    assert st.reliable_updates >= 1
+    xs = host(op.unpack(x))
+    r = b - oracle_lib.m(dims, Ls, M5, MASS, BC, U, xs)
+    assert np.linalg.norm(r) / np.linalg.norm(b) < 1e-8
+
+
 @pytest.mark.parametrize("mode", [1, 2])
 def test_mixed_cg_stopped_by_maxiter(dwf, oracle_lib, mode):
     """A mixed solve cut short by maxiter: not converged, and the returned x is the folded
